@@ -1,0 +1,466 @@
+#!/usr/bin/env python
+"""Benchmark of the coupled-Bidomain SA-AMG-PCG path on GB300.
+
+One step = one whole simulation of the paper-size slab through every row of
+the hot path: Q1 assembly of the 128x128x32 slab (1,098,306 unknowns),
+smoothed-aggregation setup, then 100 semi-implicit time steps (Rogers-McCulloch
+update + one AMG-PCG solve to rtol 1e-8 each, hierarchy reused).
+value = solves/s over all ranks (100 solves per step per rank).
+
+Arms:
+  default           the CUDA library, inputs resident in HBM, CUDA-event timing
+  --impl reference  the FP64 CPU oracle on the host cores (bounded sample of
+                    the same workload, extrapolated to the same unit)
+Multi-GPU (torchrun): independent replicas, one per GPU, no data-path
+collective; barrier + max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+T_STEPS = 100           # time steps per simulation
+STIM_MS = 1.0           # stimulus duration
+FP64_ALU_PEAK = 152 * 2 * 2 * 2.07e9   # SMs x DFMA/clk/SM x flop/FMA x max SM clock
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fine_operator_traffic.txt")
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["paper", "small", "profile"], default="paper")
+    ap.add_argument("--time-steps", type=int, default=T_STEPS)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=2)
+    ap.add_argument("--square-levels", type=int, default=None)
+    ap.add_argument("--theta", type=float, default=None)
+    ap.add_argument("--coarse-eq-limit", type=int, default=None)
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------ distributed
+def dist_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def dist_init(world, use_cuda):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend="nccl" if use_cuda else "gloo")
+    return dist
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, value: float, use_cuda: bool) -> float:
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if use_cuda else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ workload
+def workload(name):
+    from paper_2311_13914_gb300 import workloads as W
+
+    # "profile": a 96x96x24 slab whose finest operator (~0.22 GB) still exceeds L2,
+    # small enough for full ncu captures
+    mesh = {"paper": W.SLAB_PAPER, "small": W.SLAB_SMALL,
+            "profile": W.mesh(96, 96, 24, 1.0, 1.0, 0.5)}[name]
+    fib = W.fibre_table(mesh, 120.0, W.fibre_offset_from_seed(1))
+    stim = W.stimulus(mesh)
+    desc = (f"{mesh['nx']}x{mesh['ny']}x{mesh['nz']} Q1 slab {mesh['lx']}x{mesh['ly']}x{mesh['lz']} cm, "
+            f"{2 * W.n_nodes(mesh)} unknowns, assembly + SA-AMG setup + {{T}} RM time steps "
+            f"(dt 0.05 ms, corner stimulus 1 ms), one AMG-PCG solve to rtol 1e-8 per step")
+    return mesh, fib, stim, desc
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = max((float(r[2]) for r in rows if r[2].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [v for v in sm if mx and v > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": mx,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ roofline helpers
+def measured_peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except (OSError, ValueError):
+        return None
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    for f in ("amg_solve.cu", "amg_internal.cuh", "bd_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2311_13914_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per finest-level operator launch from the committed ncu
+    summary, only while the kernel source is unchanged since the capture."""
+    try:
+        kv = {}
+        for line in open(TRAFFIC_FILE):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("source_digest") != source_digest():
+            return None
+        return float(kv["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def amg_opts(B, args):
+    over = {}
+    if args.square_levels is not None:
+        over["square_levels"] = args.square_levels
+    if args.theta is not None:
+        over["theta"] = args.theta
+    if args.coarse_eq_limit is not None:
+        over["coarse_eq_limit"] = args.coarse_eq_limit
+    return B.amg_options_default(**over)
+
+
+def oracle_opts(args):
+    over = {}
+    if args.square_levels is not None:
+        over["square_levels"] = args.square_levels
+    if args.theta is not None:
+        over["theta"] = args.theta
+    if args.coarse_eq_limit is not None:
+        over["coarse_eq_limit"] = args.coarse_eq_limit
+    return over
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2311_13914_gb300 import binding as B
+    from paper_2311_13914_gb300 import workloads as W
+
+    rank, local, world = dist_info()
+    use_cuda = torch.cuda.is_available()
+    if not use_cuda:
+        raise SystemExit("bench.py (ours) needs a CUDA GPU; the library has no CPU path")
+    torch.cuda.set_device(local)
+    dist = dist_init(world, True)
+    B.lib()
+    mesh, fib, stim, desc = workload(args.workload)
+    T = args.time_steps
+    p = W.DEFAULT_PARAMS
+    N = W.n_nodes(mesh)
+    stream = torch.cuda.Stream()
+    fib_d = torch.tensor(fib.reshape(-1), device="cuda")
+    stim_d = torch.tensor(stim, device="cuda")
+    torch.cuda.synchronize()
+
+    def one_step(profile: bool, record: dict | None):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        sysh = B.bd_assemble(mesh, p, fib_d, stream=stream)
+        h = B.amg_setup(sysh, amg_opts(B, args), stream=stream)
+        ev[1].record(stream)
+        if profile:
+            B.amg_profile_enable(h, True)
+        sim = B.bd_sim_create(sysh, h, stim=stim_d, stim_ms=STIM_MS, stream=stream)
+        info = B.bd_step(sim, T, stream=stream)
+        ev[2].record(stream)
+        stream.synchronize()
+        if record is not None:
+            record["setup_ms"].append(ev[0].elapsed_time(ev[1]))
+            record["solve_ms"].append(ev[1].elapsed_time(ev[2]))
+            record["iters"].append(info["total_iters"] / max(T, 1))
+            record["true_rel_res"].append(info["true_rel_res"])
+            if profile:
+                pr = B.amg_profile_read(h)
+                for k in ("launches", "total_ms", "bytes", "flops"):
+                    record["prof_" + k] += pr[k]
+            if not record.get("levels"):
+                record["levels"] = [B.amg_level_info(h, l)["n"] for l in range(B.amg_num_levels(h))]
+                nnz = [B.amg_level_info(h, l)["nnz"] for l in range(B.amg_num_levels(h))]
+                record["op_complexity"] = sum(nnz) / nnz[0]
+        sim.close()
+        h.close()
+        sysh.close()
+        return info
+
+    for _ in range(args.warmup):
+        one_step(False, None)
+    rec = {"setup_ms": [], "solve_ms": [], "iters": [], "true_rel_res": [], "prof_launches": 0,
+           "prof_total_ms": 0.0, "prof_bytes": 0.0, "prof_flops": 0.0}
+    clocks = ClockSampler(local)
+    barrier(dist, local)
+    torch.cuda.synchronize()
+    launches0 = B.bd_launch_count()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        one_step(True, rec)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = B.bd_launch_count() - launches0
+    barrier(dist, local)
+    elapsed_ms = max_over_ranks(dist, t0.elapsed_time(t1), True)
+    value = world * args.steps * T / (elapsed_ms / 1e3)
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        fib_h = torch.tensor(fib.reshape(-1)).pin_memory()
+        stim_h = torch.tensor(stim).pin_memory()
+        v_h = torch.empty(N, dtype=torch.float64).pin_memory()
+        u_h = torch.empty(N, dtype=torch.float64).pin_memory()
+        w_h = torch.empty(N, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            sysh = B.bd_assemble(mesh, p, fib_h, stream=stream)
+            h = B.amg_setup(sysh, amg_opts(B, args), stream=stream)
+            sim = B.bd_sim_create(sysh, h, stim=stim_h, stim_ms=STIM_MS, stream=stream)
+            B.bd_step(sim, T, stream=stream)
+            B.bd_sim_get_state(sim, N, stream=stream, out=(v_h, u_h, w_h))
+            sim.close()
+            h.close()
+            sysh.close()
+
+        e2e_step()
+        barrier(dist, local)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(dist, time.perf_counter() - w0, True)
+        e2e = {"value": world * args.steps * T / e2e_s, "unit": "solves/s",
+               "h2d_bytes_per_step": fib.size * 8 + stim.size * 8,
+               "d2h_bytes_per_step": 3 * N * 8}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    prof_s = rec["prof_total_ms"] / 1e3
+    achieved_gbs = rec["prof_bytes"] / prof_s / 1e9 if prof_s > 0 else None
+    achieved_tflops = rec["prof_flops"] / prof_s / 1e12 if prof_s > 0 else None
+    t_hbm = rec["prof_bytes"] / (hbm_peak * 1e9)
+    t_alu = rec["prof_flops"] / FP64_ALU_PEAK
+    per_launch = rec["prof_bytes"] / rec["prof_launches"] if rec["prof_launches"] else None
+    traffic = recorded_traffic()
+    if t_alu > t_hbm:
+        roof = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_ALU_PEAK / 1e12,
+                "unit": "TFLOP/s", "frac": achieved_tflops / (FP64_ALU_PEAK / 1e12),
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe)"}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_peak,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"}
+    roof.update({"traffic": traffic, "kernel": "finest-level 2x2-block SpMV (fused epilogues)",
+                 "algorithmic_bytes_per_launch": per_launch, "launches": rec["prof_launches"],
+                 "hbm_gbs": achieved_gbs, "hbm_frac": achieved_gbs / hbm_peak if achieved_gbs else None,
+                 "fp64_tflops": achieved_tflops})
+    out = {
+        "metric": "AMG-PCG solves/sec to rtol 1e-8 (coupled Bidomain, paper-size slab, time stepping)",
+        "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc.format(T=T), "time_steps_per_step": T,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (finest operator 0.52 GB > 129 MB)",
+                   "setup_ms": statistics.mean(rec["setup_ms"]),
+                   "solve_only_solves_per_s": T / (statistics.mean(rec["solve_ms"]) / 1e3),
+                   "mean_pcg_iters": statistics.mean(rec["iters"]),
+                   "max_true_rel_res": max(rec["true_rel_res"]),
+                   "levels": rec.get("levels"), "operator_complexity": rec.get("op_complexity"),
+                   "amg_options": {k: getattr(amg_opts(B, args), k) for k in
+                                   ("theta", "square_levels", "coarse_eq_limit", "cheb_degree")}},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(args)
+    if dist is not None:
+        dist.destroy_process_group()
+    return out
+
+
+# ------------------------------------------------------------------ oracle (CPU)
+def oracle_sample(mesh, fib, stim, n_steps: int, opts: dict):
+    """Assembly + setup of the full workload, then n_steps time steps; returns
+    (t_setup_s, mean_step_s, mean_iters)."""
+    import numpy as np
+
+    import oracle
+    from paper_2311_13914_gb300 import workloads as W
+
+    p = W.DEFAULT_PARAMS
+    t0 = time.perf_counter()
+    o = oracle.assemble(mesh, p, fib)
+    H = oracle.Hierarchy(o["A"], **opts)
+    t_setup = time.perf_counter() - t0
+    N = W.n_nodes(mesh)
+    v, ue, w = np.zeros(N), np.zeros(N), np.zeros(N)
+    times, its = [], []
+    for k in range(n_steps):
+        Iapp = stim if k * p["dt"] < STIM_MS else np.zeros(N)
+        s0 = time.perf_counter()
+        info = H.bd_step(o["M"], p, Iapp, v, ue, w)
+        times.append(time.perf_counter() - s0)
+        its.append(info["iters"])
+    return t_setup, statistics.mean(times), statistics.mean(its)
+
+
+def cpu_baseline(args):
+    import oracle
+
+    oracle.build()
+    mesh, fib, stim, desc = workload(args.workload)
+    T = args.time_steps
+    t_setup, t_step, its = oracle_sample(mesh, fib, stim, max(1, args.cpu_sample_steps),
+                                         oracle_opts(args))
+    value = T / (t_setup + T * t_step)
+    return {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": (f"full-size assembly + setup ({t_setup:.1f} s) and the first "
+                       f"{max(1, args.cpu_sample_steps)} time steps ({t_step:.1f} s each, "
+                       f"{its:.1f} PCG its), extrapolated to {T} steps; single-threaded C oracle")}
+
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores.  Each step = one time step
+    of the same workload; assembly + setup are timed once and amortised over
+    the simulation's time steps so the unit matches the CUDA arm."""
+    import numpy as np
+
+    import oracle
+    from paper_2311_13914_gb300 import workloads as W
+
+    rank, local, world = dist_info()
+    if rank != 0:
+        return None
+    oracle.build()
+    mesh, fib, stim, desc = workload(args.workload)
+    T = args.time_steps
+    p = W.DEFAULT_PARAMS
+    t0 = time.perf_counter()
+    o = oracle.assemble(mesh, p, fib)
+    H = oracle.Hierarchy(o["A"], **oracle_opts(args))
+    t_setup = time.perf_counter() - t0
+    N = W.n_nodes(mesh)
+    v, ue, w = np.zeros(N), np.zeros(N), np.zeros(N)
+    k = 0
+
+    def step():
+        nonlocal k
+        Iapp = stim if k * p["dt"] < STIM_MS else np.zeros(N)
+        H.bd_step(o["M"], p, Iapp, v, ue, w)
+        k += 1
+
+    for _ in range(args.warmup):
+        step()
+    s0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    t_step = (time.perf_counter() - s0) / max(args.steps, 1)
+    value = T / (t_setup + T * t_step)
+    cpu = {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+           "sample": (f"assembly + setup once ({t_setup:.1f} s) and {args.steps} timed time "
+                      f"steps ({t_step:.2f} s each) of the full workload, extrapolated to "
+                      f"{T} steps")}
+    return {"impl": "reference", "metric": "AMG-PCG solves/sec to rtol 1e-8 (coupled Bidomain, "
+            "paper-size slab, time stepping)", "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc.format(T=T)},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

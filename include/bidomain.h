@@ -1,0 +1,228 @@
+/*
+ * bidomain.h -- C ABI of the GB300 (sm_103a) smoothed-aggregation AMG-PCG
+ * solver for the coupled Bidomain system of arXiv 2311.13914.
+ *
+ * The operation: every semi-implicit time step of the parabolic-elliptic
+ * Bidomain model (Section 2, Eq. 1; block form Eq. 3; time scheme Eqs. 4-7)
+ * yields one symmetric positive semi-definite system A x = f (Section 4,
+ * Eq. 9) with the interleaved 2x2-block operator
+ *     A = [c M + Ki, Ki; Ki, Ki + Ke],   c = chi*Cm/dt,
+ * whose null space is (v, u_e) = (0, 1).  It is solved by conjugate gradients
+ * preconditioned with one algebraic-multigrid V-cycle (Algorithm 2) over a
+ * smoothed-aggregation hierarchy (Algorithm 1; modified MIS, cluster rule and
+ * P_ij = |C_j|^{-1/2} of Section 4; GAMG options of Appendix A).
+ *
+ * Conventions shared by every call
+ *  - Return value: BD_OK (0) or a negative BD_E* code; bd_strerror() names it.
+ *    No call aborts, traps or exits; inputs are validated before any launch.
+ *  - Handles (bd_system, amg_hierarchy, bd_sim) are opaque, owned by the
+ *    library, released with the matching *_destroy (NULL is accepted).
+ *  - Caller arrays stay owned by the caller and are never retained after a
+ *    call returns.  Arguments named *_on_device select device pointers
+ *    (valid in the current CUDA context, ordered on `stream`) or host
+ *    pointers (pageable or pinned; the call copies them and synchronises).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls that return host-visible results synchronise `stream`.
+ *  - Node numbering of an nx*ny*nz-element slab: k = i + (nx+1)(j + (ny+1) l).
+ *    Unknowns are interleaved: x[2k] = v_k (mV), x[2k+1] = u_e,k (mV).
+ *  - Units: length cm, time ms, conductivity mS/cm, capacitance uF/cm^2,
+ *    current density uA/cm^2 (membrane) or uA/cm^3 (volumetric).
+ *  - Scalar CSR exchange format: int32 row_ptr[n+1], int32 col[nnz] (sorted
+ *    ascending within a row), double val[nnz].
+ */
+#ifndef BIDOMAIN_H
+#define BIDOMAIN_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BD_OK 0
+#define BD_EINVAL (-1)        /* invalid argument (NULL, size, layout, option)   */
+#define BD_ENOMEM (-2)        /* device or host allocation failed                */
+#define BD_ENOTCONV (-3)      /* PCG hit max_it before rtol                      */
+#define BD_EBREAKDOWN (-4)    /* PCG breakdown: p^T A p <= 0, NaN or Inf         */
+#define BD_ETIMEOUT (-5)      /* a bounded device-side loop gave up              */
+#define BD_ECUDA (-6)         /* a CUDA runtime call failed                      */
+#define BD_EINCONSISTENT (-7) /* strict mode: f not orthogonal to the null space */
+#define BD_ERANGE (-8)        /* a size exceeds a documented maximum             */
+#define BD_ESTATE (-9)        /* handle used in the wrong state                  */
+
+typedef struct bd_system bd_system;
+typedef struct amg_hierarchy amg_hierarchy;
+typedef struct bd_sim bd_sim;
+
+/* Slab [0,lx]x[0,ly]x[0,lz] (cm) meshed by nx*ny*nz uniform Q1 hexahedra. */
+typedef struct {
+    int nx, ny, nz;
+    double lx, ly, lz;
+} bd_mesh;
+
+/* chi (1/cm), Cm (uF/cm^2), dt (ms); conductivities (mS/cm) along (l) and
+ * across (t) the fibre, intracellular (i) and extracellular (e); the normal
+ * conductivity equals the transversal one (Eq. 2 with sigma_n = sigma_t). */
+typedef struct {
+    double chi, cm, dt;
+    double sil, sit, sel, set;
+} bd_params;
+
+/* Options of the hierarchy (Appendix A defaults from amg_options_default). */
+typedef struct {
+    double theta;          /* strength threshold, Section 4 (0.06)                  */
+    int coarse_eq_limit;   /* stop coarsening at <= this many unknowns (100)        */
+    int max_levels;        /* (10), at most 16                                      */
+    int cheb_degree;       /* Chebyshev-Jacobi sweeps per smoothing (2)             */
+    int esteig_steps;      /* CG steps of the lambda_max estimate (10), <= 64       */
+    int square_levels;     /* levels whose MIS runs on the squared graph (1)        */
+    double eig_lo, eig_hi; /* Chebyshev interval [eig_lo, eig_hi]*lambda (0.05,1.05) */
+    unsigned long long seed; /* MIS priorities and Lanczos start vector (0)         */
+} amg_options;
+
+typedef struct {
+    double rtol;       /* stop when ||r||_2 <= rtol ||f||_2 (1e-8)                  */
+    int max_it;        /* (500)                                                     */
+    int warm_start;    /* 1: x holds the initial guess on entry                     */
+    int strict;        /* 1: return BD_EINCONSISTENT if f has a null-space part     */
+} solve_options;
+
+typedef struct {
+    int status;          /* BD_OK, BD_ENOTCONV or BD_EBREAKDOWN                     */
+    int iters;           /* PCG iterations of this solve                            */
+    double rel_res;      /* recurrence residual / ||f||                             */
+    double true_rel_res; /* ||f - A x|| / ||f|| recomputed after the solve          */
+    double solve_ms;     /* device time of the solve (CUDA events on `stream`)      */
+    long long total_iters; /* bd_step: sum of iterations over the steps taken       */
+} solve_info;
+
+/* Rogers-McCulloch membrane model (the paper's TP06 is replaced):
+ * I_ion = G v (1 - v/vth)(1 - v/vp) + eta1 v w,  dw/dt = eta2 (v/vp - eta3 w).
+ * G, eta1 in mS/cm^2; vth, vp in mV; eta2 in 1/ms; eta3 dimensionless. */
+typedef struct {
+    double G, vth, vp, eta1, eta2, eta3;
+} bd_rm_params;
+
+const char *bd_strerror(int status);
+/* Number of CUDA kernels this library has launched in the process so far. */
+long long bd_launch_count(void);
+void amg_options_default(amg_options *o);
+void solve_options_default(solve_options *o);
+void bd_rm_params_default(bd_rm_params *p);
+
+/* ---- reproducible inner product --------------------------------------------
+ * *out = the correctly rounded value of sum_i x[i]*y[i] (each product rounded
+ * to double, the sum accumulated exactly in a fixed-point long accumulator,
+ * then rounded once to nearest-even).  The result does not depend on the
+ * launch configuration or the order of the additions; the hierarchy setup
+ * uses the same operation for its eigen-estimate (Appendix A, CG steps).
+ * x, y: n doubles, host or device; out: host.  The call allocates a small
+ * device accumulator and synchronises `stream`.  Errors: BD_EINVAL (NULL,
+ * n < 0), BD_ERANGE (n > 2^31 - 1, the accumulator's carry headroom). */
+int bd_dot_exact(const double *x, const double *y, long long n, int on_device, double *out,
+                 void *stream);
+
+/* ---- a0: Q1 assembly (Section 2.2; Eq. 2; Eq. 3) --------------------------
+ * fib: fibre unit vector a_l at the two Gauss z-levels of every element layer,
+ *   fib[(ez*2 + gz)*3 + d], d = x,y,z; gz = 0 at (ez + (1-1/sqrt3)/2)*lz/nz,
+ *   gz = 1 at (ez + (1+1/sqrt3)/2)*lz/nz; nz*6 doubles, host or device.
+ * Builds on the device: Ki, Ke (27-point), lumped mass M (N), and the block
+ * operator A in 2x2-block CSR.  Values are bit-identical to the evaluation
+ * order documented with the oracle (Gauss points ascending, elements
+ * ascending, no fused multiply-add).  Errors: BD_EINVAL (sizes < 1, lengths
+ * <= 0, NULL), BD_ERANGE (more than 2^31-1 blocks), BD_ENOMEM, BD_ECUDA. */
+int bd_assemble(const bd_mesh *mesh, const bd_params *params, const double *fib,
+                int fib_on_device, void *stream, bd_system **out);
+
+/* Sizes of an assembled system: nodes N (unknowns 2N) and scalar nnz of A. */
+int bd_system_info(const bd_system *sys, int *n_nodes, long long *nnz);
+
+/* Copy A (scalar CSR, 2N rows, sizes from bd_system_info) and M (N) to HOST
+ * arrays; any pointer may be NULL.  Synchronises `stream`. */
+int bd_system_export(const bd_system *sys, int *row_ptr, int *col, double *val,
+                     double *M, void *stream);
+
+void bd_system_destroy(bd_system *sys);
+
+/* ---- a1..a9: hierarchy setup (Algorithm 1) --------------------------------
+ * Builds, entirely with device kernels: strength graph (Section 4), squared
+ * graph on the first square_levels levels (Appendix A square_graph),
+ * hash-priority MIS, aggregates, tentative prolongator, CG-Lanczos lambda_max
+ * of D^{-1}A, smoothed prolongator P = (I - 4/(3 lambda) D^{-1}A) Pt,
+ * R = P^T, Galerkin A_c = R (A P), and a dense factor of the coarsest level.
+ * Aggregates and patterns are bit-identical to the oracle; hierarchy values
+ * follow its evaluation order.  The hierarchy is reused by every solve.
+ * Errors: BD_EINVAL, BD_ERANGE (a Galerkin row wider than 8192 blocks, or a
+ * coarsest level above 4096 unknowns), BD_ENOMEM, BD_ECUDA. */
+int amg_setup(const bd_system *sys, const amg_options *opts, void *stream, amg_hierarchy **out);
+
+/* Same from a caller matrix: n = 2N unknowns (even), interleaved 2-unknown
+ * nodes, scalar CSR whose pattern is made of full 2x2 node blocks, symmetric
+ * positive semi-definite with null vector (0,1).  Arrays host or device. */
+int amg_setup_from_csr(int n, const int *row_ptr, const int *col, const double *val,
+                       int on_device, const amg_options *opts, void *stream,
+                       amg_hierarchy **out);
+
+/* Level sizes: unknowns n, scalar nnz of A_l, aggregates built on level l
+ * (0 on the coarsest), lambda_max estimate (0 on the coarsest), and the scalar
+ * nnz of P_l (0 on the coarsest). */
+int amg_num_levels(const amg_hierarchy *h, int *nlevels);
+int amg_level_info(const amg_hierarchy *h, int level, int *n, long long *nnz, int *n_agg,
+                   double *lambda, long long *p_nnz);
+
+/* Copy level data to HOST arrays (sizes from amg_level_info; any pointer may
+ * be NULL): A_l as scalar CSR, MIS flags and aggregate ids per node, P_l as
+ * scalar CSR (n rows, 2*n_agg columns).  Synchronises `stream`. */
+int amg_export_level(const amg_hierarchy *h, int level, int *a_row_ptr, int *a_col,
+                     double *a_val, unsigned char *mis, int *agg, int *p_row_ptr,
+                     int *p_col, double *p_val, void *stream);
+
+/* ---- a10: one V-cycle z = B r (Algorithm 2) --------------------------------
+ * r, z: n doubles (host or device).  z is not projected. */
+int amg_vcycle(amg_hierarchy *h, const double *r, double *z, int on_device, void *stream);
+
+/* ---- a11: projected PCG solve of A x = f ----------------------------------
+ * f, x: n = 2N doubles, host or device.  f is projected orthogonal to (0,1)
+ * (Euclidean mean of the u_e entries removed) unless opts->strict, in which
+ * case a relative null-space part above 1e-8 returns BD_EINCONSISTENT.  On
+ * return x has mean-zero u_e.  info may be NULL.  Returns info->status. */
+int amg_solve(amg_hierarchy *h, const double *f, double *x, int on_device,
+              const solve_options *opts, void *stream, solve_info *info);
+
+void amg_destroy(amg_hierarchy *h);
+
+/* ---- live timing of the dominant kernel ------------------------------------
+ * When enabled, every application of the finest-level operator (the fused
+ * SpMV launches of the V-cycle and of PCG) is bracketed by CUDA events on the
+ * launching stream; the durations, the algorithmic bytes (matrix values and
+ * indices once, each vector stream once) and the flops (2 per scalar nonzero)
+ * are summed.  Enabling resets the sums; reading requires no pending work. */
+typedef struct {
+    long long launches;
+    double total_ms;
+    double bytes;
+    double flops;
+} amg_kernel_profile;
+int amg_profile_enable(amg_hierarchy *h, int enable);
+int amg_profile_read(const amg_hierarchy *h, amg_kernel_profile *out);
+
+/* ---- a12: time stepping (Eqs. 4-7 in coupled form) ------------------------
+ * A simulation owns device state v, u_e, w (N each, zero at creation) and
+ * borrows sys and h (which must outlive it).  stim: per-node applied current
+ * (uA/cm^3, N doubles, host or device), applied while t < stim_ms.
+ * Each step: w^{n+1} = (w + dt eta2 v/vp)/(1 + dt eta2 eta3);
+ * f = [M (c v + I_app - chi I_ion(v, w^{n+1})); 0]; solve with warm start;
+ * then t += dt.  bd_step runs nsteps steps; `last` receives the last solve
+ * plus the total iteration count. */
+int bd_sim_create(const bd_system *sys, amg_hierarchy *h, const bd_rm_params *rm,
+                  const double *stim, int stim_on_device, double stim_ms, void *stream,
+                  bd_sim **out);
+int bd_sim_set_state(bd_sim *s, const double *v, const double *ue, const double *w,
+                     int on_device, void *stream);
+int bd_sim_get_state(const bd_sim *s, double *v, double *ue, double *w, int on_device,
+                     void *stream);
+int bd_step(bd_sim *s, int nsteps, const solve_options *opts, void *stream, solve_info *last);
+void bd_sim_destroy(bd_sim *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BIDOMAIN_H */

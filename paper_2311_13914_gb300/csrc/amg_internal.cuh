@@ -1,0 +1,80 @@
+// amg_internal.cuh -- hierarchy layout shared by the setup and solve units.
+#pragma once
+
+#include "bd_common.cuh"
+
+namespace bd {
+
+constexpr int kMaxLevels = 16;
+constexpr int kMaxCoarse = 4096;   // unknowns of the dense coarsest level
+constexpr int kRedBlocks = 608;    // partial-sum blocks of the solve reductions (4 x SMs)
+
+struct Level {
+    int N = 0;                 // nodes (unknowns 2N)
+    BSR A;                     // operator
+    DBuf<double> invdiag;      // 1 / A(i,i), 2N
+    DBuf<double> B;            // near-null coefficients per field, 2N
+    DBuf<unsigned char> mis;   // root flags (not on the coarsest)
+    DBuf<int> agg;             // aggregate id per node
+    int nagg = 0;
+    double lam = 0.0;          // lambda_max(D^{-1} A) estimate
+    BSR P, R;                  // prolongator / restriction (not on the coarsest)
+    // solve workspace (double2 per node)
+    DBuf<double> f, u, r, d, w;
+    // Chebyshev coefficients (host copies)
+    double ch_inv_theta = 0, ch_c1 = 0, ch_c2 = 0;
+};
+
+// Finest level in sliced-ELL form (32 rows per slice, slot-major), using the
+// shared pattern of the Bidomain operator: per node pair only Ki and Ke are
+// stored, since the block is [Ki, Ki; Ki, Ki+Ke] off the diagonal and the
+// diagonal adds c M to the (v, v) entry.
+struct FineSell {
+    bool valid = false;
+    int nslices = 0;
+    long long slots = 0;        // padded slots (x 32 lanes)
+    DBuf<int> sptr;             // nslices + 1, slot offset of each slice
+    DBuf<int> col;              // slots * 32
+    DBuf<double> kk;            // slots * 32 * 2: (Ki, Ke)
+    DBuf<double> cm;            // c M_p per node
+};
+
+}  // namespace bd
+
+struct amg_hierarchy {
+    amg_options opts{};
+    int nlev = 0;
+    bd::FineSell sell;
+    bd::Level lev[bd::kMaxLevels];
+    // coarsest level: dense inverse of A_c + s z z^T / z^T z, null vector z
+    int nc = 0;
+    bd::DBuf<double> cinv, zc;
+    double zz = 0.0;
+    // PCG workspace on the finest level
+    bd::DBuf<double> x, r, z, p, q, fp;
+    bd::DBuf<double> partial;   // kRedBlocks x 4
+    bd::DBuf<double> scal;      // device scalars of the PCG recurrences
+    double *host_scal = nullptr;  // pinned mirror
+    bd::DBuf<long long> exact_acc;
+    // live timing of the finest-level operator applications
+    int prof = 0;
+    std::vector<cudaEvent_t> ev;      // pairs
+    std::vector<double> ev_bytes, ev_flops;
+    int ev_used = 0;
+    amg_kernel_profile prof_sum{};
+    ~amg_hierarchy() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+
+namespace bd {
+// solve-phase entry points used by bd_step (amg_solve.cu)
+int pcg_solve_device(amg_hierarchy *h, const double *f_dev, double *x_dev, int warm,
+                     const solve_options *o, cudaStream_t s, solve_info *info);
+int vcycle_device(amg_hierarchy *h, const double *r_dev, double *z_dev, cudaStream_t s);
+int prepare_solve(amg_hierarchy *h);
+int build_fine_sell(amg_hierarchy *h, const bd_system *sys, cudaStream_t s);
+int prof_begin(amg_hierarchy *h, cudaStream_t s);
+void prof_end(amg_hierarchy *h, int slot, double bytes, double flops, cudaStream_t s);
+void prof_collect(amg_hierarchy *h);
+}  // namespace bd

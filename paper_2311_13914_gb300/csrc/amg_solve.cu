@@ -1,0 +1,996 @@
+// amg_solve.cu -- a10/a11: V-cycle (Algorithm 2) with Chebyshev-Jacobi
+// smoothing (Appendix A) and the projected PCG of Section 2.2 on the device.
+//
+// Every operator application is one pass of a 2x2-block SpMV kernel whose
+// epilogue fuses the vector work of the step around it (Chebyshev recurrence,
+// residual, correction), so each level streams its matrix four times per
+// cycle and its vectors a few times.  Reductions are deterministic: fixed
+// grid, per-block partial sums, one finishing block.
+#include <algorithm>
+#include <cmath>
+#include <new>
+
+#include "amg_internal.cuh"
+
+namespace bd {
+
+// ------------------------------------------------------------------ SpMV core
+// T lanes cooperate on one 2x2 block row; the block values are read as two
+// 16-byte loads, x as one 16-byte load per block.
+template <int T, class G, class E>
+__global__ void __launch_bounds__(256) k_bsr(int N, const int *__restrict__ rp,
+                                              const int *__restrict__ ci,
+                                              const double2 *__restrict__ v, G gather, E epi)
+{
+    const int lane = threadIdx.x & (T - 1);
+    const int groups = (gridDim.x * blockDim.x) / T;
+    // warp-uniform row loop: every lane reaches the shuffles below
+    const int warp_first = ((blockIdx.x * blockDim.x + threadIdx.x) & ~31) / T;
+    const int g_in_warp = (threadIdx.x & 31) / T;
+    for (int pw = warp_first; pw < N; pw += groups) {
+        const int p = pw + g_in_warp;
+        const bool act = p < N;
+        double y0 = 0.0, y1 = 0.0;
+        const int e = act ? rp[p + 1] : 0;
+        for (int t = act ? rp[p] + lane : 0; t < e; t += T) {
+            const int q = ci[t];
+            const double2 a01 = v[2 * (size_t)t], a23 = v[2 * (size_t)t + 1];
+            const double2 x = gather(q);
+            y0 = fma(a01.x, x.x, fma(a01.y, x.y, y0));
+            y1 = fma(a23.x, x.x, fma(a23.y, x.y, y1));
+        }
+#pragma unroll
+        for (int o = T / 2; o > 0; o >>= 1) {
+            y0 += __shfl_xor_sync(0xffffffffu, y0, o, T);
+            y1 += __shfl_xor_sync(0xffffffffu, y1, o, T);
+        }
+        if (act && lane == 0) epi(p, y0, y1);
+    }
+}
+
+struct GatherVec {
+    const double2 *__restrict__ x;
+    __device__ __forceinline__ double2 operator()(int q) const { return x[q]; }
+};
+
+// pre-smoothing, degree 2 from zero, d0 = D^{-1} f / theta precomputed:
+// x1 = d0, r1 = f - A d0, d1 = c1 d0 + c2 D^{-1} r1, u = x1 + d1
+struct EpiPre {
+    const double2 *__restrict__ f;
+    const double2 *__restrict__ invd;
+    const double2 *__restrict__ d0;
+    double2 *__restrict__ u;
+    double c1, c2;
+    __device__ __forceinline__ void operator()(int p, double y0, double y1) const {
+        double2 fp = f[p], id = invd[p], dp = d0[p];
+        double r0 = fp.x - y0, r1 = fp.y - y1;
+        u[p] = make_double2(dp.x + (c1 * dp.x + c2 * id.x * r0), dp.y + (c1 * dp.y + c2 * id.y * r1));
+    }
+};
+
+// restriction output f_c = R r together with d0_c = D_c^{-1} f_c / theta_c
+struct EpiStoreD0 {
+    double2 *__restrict__ f;
+    double2 *__restrict__ d0;
+    const double2 *__restrict__ invd;
+    double it;
+    __device__ __forceinline__ void operator()(int p, double y0, double y1) const {
+        f[p] = make_double2(y0, y1);
+        double2 id = invd[p];
+        d0[p] = make_double2(y0 * id.x * it, y1 * id.y * it);
+    }
+};
+
+struct EpiResid {  // r = f - A u
+    const double2 *__restrict__ f;
+    double2 *__restrict__ r;
+    __device__ __forceinline__ void operator()(int p, double y0, double y1) const {
+        double2 fp = f[p];
+        r[p] = make_double2(fp.x - y0, fp.y - y1);
+    }
+};
+
+struct EpiStore {
+    double2 *__restrict__ y;
+    __device__ __forceinline__ void operator()(int p, double y0, double y1) const {
+        y[p] = make_double2(y0, y1);
+    }
+};
+
+struct EpiAdd {  // u += P e_c
+    double2 *__restrict__ u;
+    __device__ __forceinline__ void operator()(int p, double y0, double y1) const {
+        double2 a = u[p];
+        u[p] = make_double2(a.x + y0, a.y + y1);
+    }
+};
+
+// post-smoothing, first half: r0 = f - A u, d0 = D^{-1} r0 / theta, w = u + d0
+struct EpiPost1 {
+    const double2 *__restrict__ f;
+    const double2 *__restrict__ invd;
+    const double2 *__restrict__ u;
+    double2 *__restrict__ r;
+    double2 *__restrict__ d;
+    double2 *__restrict__ w;
+    double it;
+    __device__ __forceinline__ void operator()(int p, double y0, double y1) const {
+        double2 fp = f[p], id = invd[p], up = u[p];
+        double r0 = fp.x - y0, r1 = fp.y - y1;
+        double d0 = r0 * id.x * it, d1 = r1 * id.y * it;
+        r[p] = make_double2(r0, r1);
+        d[p] = make_double2(d0, d1);
+        w[p] = make_double2(up.x + d0, up.y + d1);
+    }
+};
+
+// post-smoothing, second half: r1 = r0 - A d0, d1 = c1 d0 + c2 D^{-1} r1, u = w + d1
+struct EpiPost2 {
+    const double2 *__restrict__ r;
+    const double2 *__restrict__ d;
+    const double2 *__restrict__ invd;
+    const double2 *__restrict__ w;
+    double2 *__restrict__ u;
+    double c1, c2;
+    __device__ __forceinline__ void operator()(int p, double y0, double y1) const {
+        double2 rp_ = r[p], dp = d[p], id = invd[p], wp = w[p];
+        double r0 = rp_.x - y0, r1 = rp_.y - y1;
+        u[p] = make_double2(wp.x + (c1 * dp.x + c2 * id.x * r0), wp.y + (c1 * dp.y + c2 * id.y * r1));
+    }
+};
+
+template <class G, class E>
+static int launch_bsr(const BSR &A, int T, G g, E e, cudaStream_t s)
+{
+    int N = A.nbr;
+    if (N <= 0) return BD_OK;
+    const int threads = 256;
+    long long groups_per_block = threads / T;
+    int grid = (int)std::min<long long>((N + groups_per_block - 1) / groups_per_block, (long long)kSM * 16);
+    const double2 *v = (const double2 *)A.v.p;
+    switch (T) {
+    case 1: k_bsr<1><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, v, g, e); ::bd::note_launch(); break;
+    case 2: k_bsr<2><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, v, g, e); ::bd::note_launch(); break;
+    case 4: k_bsr<4><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, v, g, e); ::bd::note_launch(); break;
+    case 8: k_bsr<8><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, v, g, e); ::bd::note_launch(); break;
+    case 16: k_bsr<16><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, v, g, e); ::bd::note_launch(); break;
+    default: k_bsr<32><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, v, g, e); ::bd::note_launch(); break;
+    }
+    BD_LAUNCH_CHECK();
+    return BD_OK;
+}
+
+// Lanes per block row.  Every lane-level reduction step costs FP64 adds, which
+// are scarce on this part, so rows are handled by as few lanes as their length
+// allows (one thread per row for short rows); small levels get more lanes per
+// row so that the grid still fills the GPU.
+static int lanes_for(const BSR &A)
+{
+    double avg = A.nbr > 0 ? (double)A.nb / A.nbr : 1.0;
+    int T = avg <= 40 ? 1 : (avg <= 160 ? 4 : (avg <= 640 ? 8 : 16));
+    while (T < 32 && (long long)A.nbr * T < 65536) T <<= 1;
+    return T;
+}
+
+// ------------------------------------------------------------------ finest level, sliced ELL
+// One thread per row; slot j of slice s holds entry j of its 32 rows
+// contiguously, so every slot is one coalesced 512-byte (Ki, Ke) load and one
+// 128-byte column load per warp.  Per node pair: s = v_q + u_q,
+// a += Ki s, b += Ke u_q (three FP64 operations, 20 bytes); then
+// y_v = c M_p v_p + a, y_u = a + b.
+template <class G, class E>
+__global__ void __launch_bounds__(256) k_sell(int N, const int *__restrict__ sptr,
+                                               const int *__restrict__ col,
+                                               const double2 *__restrict__ kk,
+                                               const double *__restrict__ cm, G gather, E epi)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
+        const int sl = p >> 5, lane = p & 31;
+        const int j1 = sptr[sl + 1];
+        double a = 0.0, b = 0.0;
+        for (int j = sptr[sl]; j < j1; j++) {
+            const size_t idx = (size_t)j * 32 + lane;
+            const int q = col[idx];
+            const double2 k = kk[idx];
+            const double2 x = gather(q);
+            a = fma(k.x, x.x + x.y, a);
+            b = fma(k.y, x.y, b);
+        }
+        const double2 xp = gather(p);
+        epi(p, fma(cm[p], xp.x, a), a + b);
+    }
+}
+
+__global__ void k_sell_width(int N, const int *__restrict__ rp, int *__restrict__ w, int nslices)
+{
+    int sl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl >= nslices) return;
+    int mx = 0;
+    for (int p = sl * 32; p < sl * 32 + 32 && p < N; p++) mx = max(mx, rp[p + 1] - rp[p]);
+    w[sl] = mx;
+}
+
+__global__ void k_sell_fill(int N, const int *__restrict__ rp, const int *__restrict__ ci,
+                            const double *__restrict__ Ki, const double *__restrict__ Ke,
+                            const double *__restrict__ M, double c, const int *__restrict__ sptr,
+                            int *__restrict__ col, double2 *__restrict__ kk, double *__restrict__ cm)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    int sl = p >> 5, lane = p & 31;
+    int j0 = sptr[sl], width = sptr[sl + 1] - j0, b = rp[p], len = rp[p + 1] - b;
+    for (int j = 0; j < width; j++) {
+        size_t idx = (size_t)(j0 + j) * 32 + lane;
+        if (j < len) {
+            col[idx] = ci[b + j];
+            kk[idx] = make_double2(Ki[b + j], Ke[b + j]);
+        } else {
+            col[idx] = p;
+            kk[idx] = make_double2(0.0, 0.0);
+        }
+    }
+    cm[p] = c * M[p];
+}
+
+int build_fine_sell(amg_hierarchy *h, const bd_system *sys, cudaStream_t s)
+{
+    FineSell &F = h->sell;
+    const int N = sys->N;
+    F.nslices = (N + 31) / 32;
+    DBuf<int> w;
+    BD_TRY(w.alloc((size_t)F.nslices + 1));
+    BD_TRY(F.sptr.alloc((size_t)F.nslices + 1));
+    k_sell_width<<<(F.nslices + 255) / 256, 256, 0, s>>>(N, sys->A.rp.p, w.p, F.nslices); ::bd::note_launch();
+    BD_LAUNCH_CHECK();
+    long long slots = 0;
+    BD_TRY(exclusive_scan(w.p, F.sptr.p, F.nslices, &slots, s));
+    F.slots = slots;
+    BD_TRY(F.col.alloc((size_t)slots * 32));
+    BD_TRY(F.kk.alloc((size_t)slots * 64));
+    BD_TRY(F.cm.alloc((size_t)N));
+    const bd_params &P = sys->params;
+    k_sell_fill<<<(N + 255) / 256, 256, 0, s>>>(N, sys->A.rp.p, sys->A.ci.p, sys->Ki.p, sys->Ke.p,
+                                                sys->M.p, (P.chi * P.cm) / P.dt, F.sptr.p, F.col.p,
+                                                (double2 *)F.kk.p, F.cm.p); ::bd::note_launch();
+    BD_LAUNCH_CHECK();
+    BD_CUDA(cudaStreamSynchronize(s));
+    F.valid = true;
+    return BD_OK;
+}
+
+// operator application of level l: sliced ELL on the finest level when
+// available, 2x2-block CSR otherwise
+template <class G, class E>
+static int apply_level(amg_hierarchy *h, int l, G g, E e, cudaStream_t s)
+{
+    const Level &L = h->lev[l];
+    if (l == 0 && h->sell.valid) {
+        const FineSell &F = h->sell;
+        int grid = (int)std::min<long long>(((long long)L.N + 255) / 256, (long long)kSM * 8);
+        k_sell<<<grid, 256, 0, s>>>(L.N, F.sptr.p, F.col.p, (const double2 *)F.kk.p, F.cm.p, g, e); ::bd::note_launch();
+        BD_LAUNCH_CHECK();
+        return BD_OK;
+    }
+    return launch_bsr(L.A, lanes_for(L.A), g, e, s);
+}
+
+// ------------------------------------------------------------------ live kernel timing
+int prof_begin(amg_hierarchy *h, cudaStream_t s)
+{
+    if (!h->prof) return -1;
+    if (h->ev_used * 2 + 2 > (int)h->ev.size()) {
+        if (h->ev.size() >= 8192) prof_collect(h);  // bounded pool: drain (synchronises)
+        while (h->ev_used * 2 + 2 > (int)h->ev.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            h->ev.push_back(e);
+            h->ev_bytes.push_back(0.0);
+            h->ev_flops.push_back(0.0);
+        }
+    }
+    int slot = h->ev_used++;
+    cudaEventRecord(h->ev[2 * slot], s);
+    return slot;
+}
+
+void prof_end(amg_hierarchy *h, int slot, double bytes, double flops, cudaStream_t s)
+{
+    if (slot < 0) return;
+    cudaEventRecord(h->ev[2 * slot + 1], s);
+    h->ev_bytes[slot] = bytes;
+    h->ev_flops[slot] = flops;
+}
+
+void prof_collect(amg_hierarchy *h)
+{
+    for (int i = 0; i < h->ev_used; i++) {
+        cudaEventSynchronize(h->ev[2 * i + 1]);
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]) == cudaSuccess) {
+            h->prof_sum.launches++;
+            h->prof_sum.total_ms += ms;
+            h->prof_sum.bytes += h->ev_bytes[i];
+            h->prof_sum.flops += h->ev_flops[i];
+        }
+    }
+    h->ev_used = 0;
+}
+
+// Algorithmic bytes of one finest-level operator application: the stored
+// matrix once (sliced ELL: 20 bytes per slot incl. padding, plus slice offsets
+// and c M; block CSR: 36 bytes per block plus row offsets) and `vec16` 16-byte
+// per-node vector streams.  Flops: 2 per scalar nonzero (8 per 2x2 block).
+static double fine_bytes(const amg_hierarchy *h, const Level &L, int vec16)
+{
+    double mat = h->sell.valid
+                     ? 20.0 * 32.0 * (double)h->sell.slots + 4.0 * (h->sell.nslices + 1) + 8.0 * L.N
+                     : 36.0 * (double)L.A.nb + 4.0 * (L.N + 1);
+    return mat + 16.0 * vec16 * (double)L.N;
+}
+static double fine_flops(const amg_hierarchy *, const Level &L) { return 8.0 * (double)L.A.nb; }
+
+// ------------------------------------------------------------------ coarsest level
+// x = Cinv (r - (z.r / z.z) z); one block, one warp per output row.
+__global__ void k_coarse_solve(int n, const double *__restrict__ cinv, const double *__restrict__ z,
+                               double zz, const double *__restrict__ r, double *__restrict__ x)
+{
+    extern __shared__ double rs[];
+    __shared__ double red[32];
+    double part = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) part += z[i] * r[i];
+    for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) red[0] = v;
+    }
+    __syncthreads();
+    double a = zz > 0.0 ? red[0] / zz : 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) rs[i] = r[i] - a * z[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < n; i += nw) {
+        const double *row = cinv + (size_t)i * n;
+        double sacc = 0.0;
+        for (int j = lane; j < n; j += 32) sacc += row[j] * rs[j];
+        for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+        if (lane == 0) x[i] = sacc;
+    }
+}
+
+__global__ void k_copy2(int N, const double2 *__restrict__ a, double2 *__restrict__ b)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) b[i] = a[i];
+}
+
+__global__ void k_scale_d0(int N, const double2 *__restrict__ f, const double2 *__restrict__ invd,
+                           double it, double2 *__restrict__ u)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        double2 a = f[i], b = invd[i];
+        u[i] = make_double2(a.x * b.x * it, a.y * b.y * it);
+    }
+}
+
+int vcycle_device(amg_hierarchy *h, const double *r_dev, double *z_dev, cudaStream_t s)
+{
+    const int nl = h->nlev;
+    const bool deg2 = h->opts.cheb_degree == 2;
+    for (int l = 0; l < nl - 1; l++) {
+        Level &L = h->lev[l];
+        const double2 *f = (const double2 *)(l == 0 ? r_dev : L.f.p);
+        double2 *u = (double2 *)(l == 0 ? z_dev : L.u.p);
+        const double2 *invd = (const double2 *)L.invdiag.p;
+        double2 *d0 = (double2 *)L.d.p;
+        if (l == 0) {  // coarser levels receive d0 from the restriction epilogue
+            k_scale_d0<<<grid_for(L.N, 256), 256, 0, s>>>(L.N, f, invd, L.ch_inv_theta, d0); ::bd::note_launch();
+            BD_LAUNCH_CHECK();
+        }
+        if (deg2) {
+            int sl = l == 0 ? prof_begin(h, s) : -1;
+            BD_TRY(apply_level(h, l, GatherVec{d0}, EpiPre{f, invd, d0, u, L.ch_c1, L.ch_c2}, s));
+            prof_end(h, sl, fine_bytes(h, L, 4), fine_flops(h, L), s);
+        } else {
+            k_copy2<<<grid_for(L.N, 256), 256, 0, s>>>(L.N, d0, u); ::bd::note_launch();
+            BD_LAUNCH_CHECK();
+        }
+        int sr = l == 0 ? prof_begin(h, s) : -1;
+        BD_TRY(apply_level(h, l, GatherVec{u}, EpiResid{f, (double2 *)L.r.p}, s));
+        prof_end(h, sr, fine_bytes(h, L, 3), fine_flops(h, L), s);
+        Level &C = h->lev[l + 1];
+        BD_TRY(launch_bsr(L.R, lanes_for(L.R), GatherVec{(const double2 *)L.r.p},
+                          EpiStoreD0{(double2 *)C.f.p, (double2 *)C.d.p,
+                                     (const double2 *)C.invdiag.p, C.ch_inv_theta},
+                          s));
+    }
+    {
+        Level &C = h->lev[nl - 1];
+        const double *f = nl == 1 ? r_dev : C.f.p;
+        double *u = nl == 1 ? z_dev : C.u.p;
+        size_t smem = sizeof(double) * (size_t)h->nc;
+        k_coarse_solve<<<1, 1024, smem, s>>>(h->nc, h->cinv.p, h->zc.p, h->zz, f, u); ::bd::note_launch();
+        BD_LAUNCH_CHECK();
+    }
+    for (int l = nl - 2; l >= 0; l--) {
+        Level &L = h->lev[l];
+        const double2 *f = (const double2 *)(l == 0 ? r_dev : L.f.p);
+        double2 *u = (double2 *)(l == 0 ? z_dev : L.u.p);
+        const double2 *invd = (const double2 *)L.invdiag.p;
+        BD_TRY(launch_bsr(L.P, lanes_for(L.P), GatherVec{(const double2 *)h->lev[l + 1].u.p}, EpiAdd{u}, s));
+        int s1 = l == 0 ? prof_begin(h, s) : -1;
+        BD_TRY(apply_level(h, l, GatherVec{u},
+                           EpiPost1{f, invd, u, (double2 *)L.r.p, (double2 *)L.d.p, (double2 *)L.w.p,
+                                    L.ch_inv_theta},
+                           s));
+        prof_end(h, s1, fine_bytes(h, L, 6), fine_flops(h, L), s);
+        if (deg2) {
+            int s2 = l == 0 ? prof_begin(h, s) : -1;
+            BD_TRY(apply_level(h, l, GatherVec{(const double2 *)L.d.p},
+                               EpiPost2{(const double2 *)L.r.p, (const double2 *)L.d.p, invd,
+                                        (const double2 *)L.w.p, u, L.ch_c1, L.ch_c2},
+                               s));
+            prof_end(h, s2, fine_bytes(h, L, 5), fine_flops(h, L), s);
+        } else {
+            k_copy2<<<grid_for(L.N, 256), 256, 0, s>>>(L.N, (const double2 *)L.w.p, u); ::bd::note_launch();
+            BD_LAUNCH_CHECK();
+        }
+    }
+    return BD_OK;
+}
+
+// ------------------------------------------------------------------ PCG reductions
+// scal[] slots of the device scalars
+enum {
+    S_SUMFU = 0, S_FF, S_NF2, S_RR, S_RZ, S_RZOLD, S_PQ, S_ALPHA, S_BETA, S_MEANZ,
+    S_SUMRU, S_BREAK, S_MEANF, S_TRR, S_MEANX, S_NSLOTS
+};
+
+__device__ __forceinline__ void block_partials(double a, double b, double c, double *partial)
+{
+    __shared__ double red[3][32];
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        red[0][w] = a;
+        red[1][w] = b;
+        red[2][w] = c;
+    }
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        a = l < nw ? red[0][l] : 0.0;
+        b = l < nw ? red[1][l] : 0.0;
+        c = l < nw ? red[2][l] : 0.0;
+        for (int o = 16; o; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+        if (l == 0) {
+            partial[3 * blockIdx.x + 0] = a;
+            partial[3 * blockIdx.x + 1] = b;
+            partial[3 * blockIdx.x + 2] = c;
+        }
+    }
+}
+
+// Reduce the kRedBlocks partial triples in a fixed order, then apply `stage`.
+__global__ void k_finish(const double *__restrict__ partial, int nparts, double *scal, int stage,
+                         int N, int first)
+{
+    __shared__ double red[3][32];
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        a += partial[3 * i];
+        b += partial[3 * i + 1];
+        c += partial[3 * i + 2];
+    }
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        red[0][w] = a;
+        red[1][w] = b;
+        red[2][w] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    a = b = c = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
+        a += red[0][i];
+        b += red[1][i];
+        c += red[2][i];
+    }
+    switch (stage) {
+    case 0:  // f statistics: sum f_u, ||f||^2
+        scal[S_SUMFU] = a;
+        scal[S_FF] = b;
+        scal[S_MEANF] = a / N;
+        break;
+    case 1:  // ||fp||^2
+        scal[S_NF2] = a;
+        break;
+    case 2:  // ||r||^2
+        scal[S_RR] = a;
+        break;
+    case 3: {  // z statistics: sum z_u, sum r_u, r.z
+        double mz = a / N;
+        double rz = c - mz * b;
+        scal[S_MEANZ] = mz;
+        scal[S_BETA] = first ? 0.0 : rz / scal[S_RZ];
+        scal[S_RZ] = rz;
+        break;
+    }
+    case 4: {  // p.q
+        scal[S_PQ] = a;
+        if (!(a > 0.0) || !isfinite(a) || !isfinite(scal[S_RZ])) scal[S_BREAK] = 1.0;
+        scal[S_ALPHA] = scal[S_RZ] / a;
+        break;
+    }
+    case 5:  // true residual and mean of x_u
+        scal[S_TRR] = a;
+        scal[S_MEANX] = b / N;
+        break;
+    }
+}
+
+__global__ void k_f_stats(int N, const double2 *__restrict__ f, double *partial)
+{
+    double a = 0.0, b = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        double2 v = f[i];
+        a += v.y;
+        b += v.x * v.x + v.y * v.y;
+    }
+    block_partials(a, b, 0.0, partial);
+}
+
+__global__ void k_project_f(int N, const double2 *__restrict__ f, const double *__restrict__ scal,
+                            double2 *__restrict__ fp, double *partial)
+{
+    double m = scal[S_MEANF], a = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        double2 v = f[i];
+        v.y -= m;
+        fp[i] = v;
+        a += v.x * v.x + v.y * v.y;
+    }
+    block_partials(a, 0.0, 0.0, partial);
+}
+
+__global__ void k_zero2(int N, double2 *x)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        x[i] = make_double2(0.0, 0.0);
+}
+
+// r = f - A x with ||r||^2 partials (one row per thread group; the epilogue
+// accumulates into a per-thread register that the block reduces at the end)
+template <int T>
+__global__ void __launch_bounds__(256) k_resid_norm(int N, const int *__restrict__ rp,
+                                                     const int *__restrict__ ci,
+                                                     const double2 *__restrict__ v,
+                                                     const double2 *__restrict__ x,
+                                                     const double2 *__restrict__ f,
+                                                     double2 *__restrict__ r, double *partial,
+                                                     int want_xmean)
+{
+    const int lane = threadIdx.x & (T - 1);
+    const int groups = (gridDim.x * blockDim.x) / T;
+    const int warp_first = ((blockIdx.x * blockDim.x + threadIdx.x) & ~31) / T;
+    const int g_in_warp = (threadIdx.x & 31) / T;
+    double acc = 0.0, xs = 0.0;
+    for (int pw = warp_first; pw < N; pw += groups) {
+        const int p = pw + g_in_warp;
+        const bool act = p < N;
+        double y0 = 0.0, y1 = 0.0;
+        const int e = act ? rp[p + 1] : 0;
+        for (int t = act ? rp[p] + lane : 0; t < e; t += T) {
+            const int q = ci[t];
+            const double2 a01 = v[2 * (size_t)t], a23 = v[2 * (size_t)t + 1];
+            const double2 xq = x[q];
+            y0 = fma(a01.x, xq.x, fma(a01.y, xq.y, y0));
+            y1 = fma(a23.x, xq.x, fma(a23.y, xq.y, y1));
+        }
+#pragma unroll
+        for (int o = T / 2; o > 0; o >>= 1) {
+            y0 += __shfl_xor_sync(0xffffffffu, y0, o, T);
+            y1 += __shfl_xor_sync(0xffffffffu, y1, o, T);
+        }
+        if (act && lane == 0) {
+            double2 fp = f[p];
+            double r0 = fp.x - y0, r1 = fp.y - y1;
+            if (r) r[p] = make_double2(r0, r1);
+            acc += r0 * r0 + r1 * r1;
+            if (want_xmean) xs += x[p].y;
+        }
+    }
+    block_partials(acc, xs, 0.0, partial);
+}
+
+// q = A p with p.q partials
+template <int T>
+__global__ void __launch_bounds__(256) k_apply_dot(int N, const int *__restrict__ rp,
+                                                    const int *__restrict__ ci,
+                                                    const double2 *__restrict__ v,
+                                                    const double2 *__restrict__ p_,
+                                                    double2 *__restrict__ q, double *partial)
+{
+    const int lane = threadIdx.x & (T - 1);
+    const int groups = (gridDim.x * blockDim.x) / T;
+    const int warp_first = ((blockIdx.x * blockDim.x + threadIdx.x) & ~31) / T;
+    const int g_in_warp = (threadIdx.x & 31) / T;
+    double acc = 0.0;
+    for (int pw = warp_first; pw < N; pw += groups) {
+        const int p = pw + g_in_warp;
+        const bool act = p < N;
+        double y0 = 0.0, y1 = 0.0;
+        const int e = act ? rp[p + 1] : 0;
+        for (int t = act ? rp[p] + lane : 0; t < e; t += T) {
+            const int c = ci[t];
+            const double2 a01 = v[2 * (size_t)t], a23 = v[2 * (size_t)t + 1];
+            const double2 xq = p_[c];
+            y0 = fma(a01.x, xq.x, fma(a01.y, xq.y, y0));
+            y1 = fma(a23.x, xq.x, fma(a23.y, xq.y, y1));
+        }
+#pragma unroll
+        for (int o = T / 2; o > 0; o >>= 1) {
+            y0 += __shfl_xor_sync(0xffffffffu, y0, o, T);
+            y1 += __shfl_xor_sync(0xffffffffu, y1, o, T);
+        }
+        if (act && lane == 0) {
+            q[p] = make_double2(y0, y1);
+            double2 pp = p_[p];
+            acc += pp.x * y0 + pp.y * y1;
+        }
+    }
+    block_partials(acc, 0.0, 0.0, partial);
+}
+
+__global__ void k_z_stats(int N, const double2 *__restrict__ z, const double2 *__restrict__ r,
+                          double *partial)
+{
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        double2 zi = z[i], ri = r[i];
+        a += zi.y;
+        b += ri.y;
+        c += ri.x * zi.x + ri.y * zi.y;
+    }
+    block_partials(a, b, c, partial);
+}
+
+// p = z (first iteration: p holds no previous direction) or p = z + beta p
+__global__ void k_p_update(int N, double2 *__restrict__ z, double2 *__restrict__ p,
+                           const double *__restrict__ scal, int first)
+{
+    double mz = scal[S_MEANZ], beta = scal[S_BETA];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        double2 zi = z[i];
+        zi.y -= mz;
+        z[i] = zi;
+        if (first) {
+            p[i] = zi;
+        } else {
+            double2 pi = p[i];
+            p[i] = make_double2(zi.x + beta * pi.x, zi.y + beta * pi.y);
+        }
+    }
+}
+
+__global__ void k_xr_update(int N, double2 *__restrict__ x, double2 *__restrict__ r,
+                            const double2 *__restrict__ p, const double2 *__restrict__ q,
+                            const double *__restrict__ scal, double *partial)
+{
+    double alpha = scal[S_ALPHA], acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        double2 xi = x[i], ri = r[i], pi = p[i], qi = q[i];
+        xi.x += alpha * pi.x;
+        xi.y += alpha * pi.y;
+        ri.x -= alpha * qi.x;
+        ri.y -= alpha * qi.y;
+        x[i] = xi;
+        r[i] = ri;
+        acc += ri.x * ri.x + ri.y * ri.y;
+    }
+    block_partials(acc, 0.0, 0.0, partial);
+}
+
+__global__ void k_project_x(int N, double2 *__restrict__ x, const double *__restrict__ scal)
+{
+    double m = scal[S_MEANX];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) x[i].y -= m;
+}
+
+// Sliced-ELL finest-level operator with a reduction epilogue.
+// MODE 0: out = A x, partial x.(A x).  MODE 1: out = f - A x (if out), partials
+// ||f - A x||^2 and sum of x_u.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_sell_reduce(int N, const int *__restrict__ sptr,
+                                                      const int *__restrict__ col,
+                                                      const double2 *__restrict__ kk,
+                                                      const double *__restrict__ cm,
+                                                      const double2 *__restrict__ x,
+                                                      const double2 *__restrict__ f,
+                                                      double2 *__restrict__ out, double *partial)
+{
+    double acc = 0.0, xs = 0.0;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
+        const int sl = p >> 5, lane = p & 31;
+        const int j1 = sptr[sl + 1];
+        double a = 0.0, b = 0.0;
+        for (int j = sptr[sl]; j < j1; j++) {
+            const size_t idx = (size_t)j * 32 + lane;
+            const int q = col[idx];
+            const double2 k = kk[idx];
+            const double2 xq = x[q];
+            a = fma(k.x, xq.x + xq.y, a);
+            b = fma(k.y, xq.y, b);
+        }
+        const double2 xp = x[p];
+        const double y0 = fma(cm[p], xp.x, a), y1 = a + b;
+        if (MODE == 0) {
+            out[p] = make_double2(y0, y1);
+            acc += xp.x * y0 + xp.y * y1;
+        } else {
+            const double2 fp = f[p];
+            const double r0 = fp.x - y0, r1 = fp.y - y1;
+            if (out) out[p] = make_double2(r0, r1);
+            acc += r0 * r0 + r1 * r1;
+            xs += xp.y;
+        }
+    }
+    block_partials(acc, xs, 0.0, partial);
+}
+
+template <int T>
+static void launch_resid_norm(const BSR &A, const double2 *x, const double2 *f, double2 *r,
+                              double *partial, int want_xmean, cudaStream_t s)
+{
+    k_resid_norm<T><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, (const double2 *)A.v.p, x, f, r,
+                                               partial, want_xmean); ::bd::note_launch();
+}
+
+template <int T>
+static void launch_apply_dot(const BSR &A, const double2 *p, double2 *q, double *partial, cudaStream_t s)
+{
+    k_apply_dot<T><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, (const double2 *)A.v.p, p, q, partial); ::bd::note_launch();
+}
+
+static void resid_norm(const amg_hierarchy *h, const BSR &A, int T, const double2 *x,
+                       const double2 *f, double2 *r, double *partial, int want_xmean, cudaStream_t s)
+{
+    if (h->sell.valid) {
+        const FineSell &F = h->sell;
+        k_sell_reduce<1><<<kRedBlocks, 256, 0, s>>>(A.nbr, F.sptr.p, F.col.p, (const double2 *)F.kk.p,
+                                                    F.cm.p, x, f, r, partial); ::bd::note_launch();
+        return;
+    }
+    switch (T) {
+    case 1: launch_resid_norm<1>(A, x, f, r, partial, want_xmean, s); break;
+    case 2: launch_resid_norm<2>(A, x, f, r, partial, want_xmean, s); break;
+    case 4: launch_resid_norm<4>(A, x, f, r, partial, want_xmean, s); break;
+    case 8: launch_resid_norm<8>(A, x, f, r, partial, want_xmean, s); break;
+    case 16: launch_resid_norm<16>(A, x, f, r, partial, want_xmean, s); break;
+    default: launch_resid_norm<32>(A, x, f, r, partial, want_xmean, s); break;
+    }
+}
+
+static void apply_dot(const amg_hierarchy *h, const BSR &A, int T, const double2 *p, double2 *q,
+                      double *partial, cudaStream_t s)
+{
+    if (h->sell.valid) {
+        const FineSell &F = h->sell;
+        k_sell_reduce<0><<<kRedBlocks, 256, 0, s>>>(A.nbr, F.sptr.p, F.col.p, (const double2 *)F.kk.p,
+                                                    F.cm.p, p, nullptr, q, partial); ::bd::note_launch();
+        return;
+    }
+    switch (T) {
+    case 1: launch_apply_dot<1>(A, p, q, partial, s); break;
+    case 2: launch_apply_dot<2>(A, p, q, partial, s); break;
+    case 4: launch_apply_dot<4>(A, p, q, partial, s); break;
+    case 8: launch_apply_dot<8>(A, p, q, partial, s); break;
+    case 16: launch_apply_dot<16>(A, p, q, partial, s); break;
+    default: launch_apply_dot<32>(A, p, q, partial, s); break;
+    }
+}
+
+int prepare_solve(amg_hierarchy *h)
+{
+    for (int l = 0; l < h->nlev; l++) {
+        Level &L = h->lev[l];
+        size_t n = 2 * (size_t)L.N;
+        BD_TRY(L.f.alloc(n));
+        BD_TRY(L.u.alloc(n));
+        BD_TRY(L.r.alloc(n));
+        BD_TRY(L.d.alloc(n));
+        BD_TRY(L.w.alloc(n));
+        if (l < h->nlev - 1) {
+            double lo = h->opts.eig_lo * L.lam, hi = h->opts.eig_hi * L.lam;
+            double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+            double sigma = theta / delta, rho0 = 1.0 / sigma;
+            double rho1 = 1.0 / (2.0 * sigma - rho0);
+            L.ch_inv_theta = 1.0 / theta;
+            L.ch_c1 = rho1 * rho0;
+            L.ch_c2 = 2.0 * rho1 / delta;
+        }
+    }
+    size_t n0 = 2 * (size_t)h->lev[0].N;
+    BD_TRY(h->x.alloc(n0));
+    BD_TRY(h->r.alloc(n0));
+    BD_TRY(h->z.alloc(n0));
+    BD_TRY(h->p.alloc(n0));
+    BD_TRY(h->q.alloc(n0));
+    BD_TRY(h->fp.alloc(n0));
+    BD_TRY(h->partial.alloc(3 * (size_t)kRedBlocks));
+    BD_TRY(h->scal.alloc(S_NSLOTS));
+    if (!h->host_scal) BD_CUDA(cudaMallocHost((void **)&h->host_scal, sizeof(double) * S_NSLOTS));
+    return BD_OK;
+}
+
+static int read_scal(amg_hierarchy *h, cudaStream_t s)
+{
+    BD_CUDA(cudaMemcpyAsync(h->host_scal, h->scal.p, sizeof(double) * S_NSLOTS, cudaMemcpyDeviceToHost, s));
+    BD_CUDA(cudaStreamSynchronize(s));
+    return BD_OK;
+}
+
+// Projected PCG on device vectors (f_dev, x_dev: 2N doubles each).
+int pcg_solve_device(amg_hierarchy *h, const double *f_dev, double *x_dev, int warm,
+                     const solve_options *o, cudaStream_t s, solve_info *info)
+{
+    Level &L0 = h->lev[0];
+    const int N = L0.N;
+    const int T = lanes_for(L0.A);
+    double2 *x = (double2 *)x_dev, *r = (double2 *)h->r.p, *z = (double2 *)h->z.p;
+    double2 *p = (double2 *)h->p.p, *q = (double2 *)h->q.p, *fp = (double2 *)h->fp.p;
+    double *part = h->partial.p, *scal = h->scal.p;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BD_CUDA(cudaEventCreate(&e0));
+    BD_CUDA(cudaEventCreate(&e1));
+    BD_CUDA(cudaEventRecord(e0, s));
+    BD_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * S_NSLOTS, s));
+    const int G = kRedBlocks;
+    k_f_stats<<<G, 256, 0, s>>>(N, (const double2 *)f_dev, part); ::bd::note_launch();
+    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 0, N, 0); ::bd::note_launch();
+    k_project_f<<<G, 256, 0, s>>>(N, (const double2 *)f_dev, scal, fp, part); ::bd::note_launch();
+    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 1, N, 0); ::bd::note_launch();
+    if (!warm) k_zero2<<<G, 256, 0, s>>>(N, x); ::bd::note_launch();
+    resid_norm(h, L0.A, T, x, fp, r, part, 0, s);
+    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 2, N, 0); ::bd::note_launch();
+    BD_LAUNCH_CHECK();
+    BD_TRY(read_scal(h, s));
+    double ff = h->host_scal[S_FF], sumfu = h->host_scal[S_SUMFU];
+    double nf = sqrt(h->host_scal[S_NF2]);
+    double rr = sqrt(h->host_scal[S_RR]);
+    int status = BD_OK, it = 0;
+    if (o->strict && ff > 0.0) {
+        double null_part = fabs(sumfu) / sqrt((double)N);
+        if (null_part > 1e-8 * sqrt(ff)) status = BD_EINCONSISTENT;
+    }
+    if (status == BD_OK && nf == 0.0) {
+        k_zero2<<<G, 256, 0, s>>>(N, x); ::bd::note_launch();
+        BD_LAUNCH_CHECK();
+        rr = 0.0;
+    } else if (status == BD_OK && !(rr <= o->rtol * nf)) {
+        status = BD_ENOTCONV;
+        while (it < o->max_it) {
+            BD_TRY(vcycle_device(h, (const double *)r, (double *)z, s));
+            k_z_stats<<<G, 256, 0, s>>>(N, z, r, part); ::bd::note_launch();
+            k_finish<<<1, 1024, 0, s>>>(part, G, scal, 3, N, it == 0); ::bd::note_launch();
+            k_p_update<<<G, 256, 0, s>>>(N, z, p, scal, it == 0); ::bd::note_launch();
+            int sq = prof_begin(h, s);
+            apply_dot(h, L0.A, T, p, q, part, s);
+            prof_end(h, sq, fine_bytes(h, L0, 2), fine_flops(h, L0), s);
+            k_finish<<<1, 1024, 0, s>>>(part, G, scal, 4, N, 0); ::bd::note_launch();
+            k_xr_update<<<G, 256, 0, s>>>(N, x, r, p, q, scal, part); ::bd::note_launch();
+            k_finish<<<1, 1024, 0, s>>>(part, G, scal, 2, N, 0); ::bd::note_launch();
+            BD_LAUNCH_CHECK();
+            BD_TRY(read_scal(h, s));
+            it++;
+            if (h->host_scal[S_BREAK] != 0.0) {
+                status = BD_EBREAKDOWN;
+                break;
+            }
+            rr = sqrt(h->host_scal[S_RR]);
+            if (!std::isfinite(rr)) {
+                status = BD_EBREAKDOWN;
+                break;
+            }
+            if (rr <= o->rtol * nf) {
+                status = BD_OK;
+                break;
+            }
+        }
+    }
+    // true residual and projection of x
+    resid_norm(h, L0.A, T, x, fp, nullptr, part, 1, s);
+    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 5, N, 0); ::bd::note_launch();
+    k_project_x<<<G, 256, 0, s>>>(N, x, scal); ::bd::note_launch();
+    BD_LAUNCH_CHECK();
+    BD_CUDA(cudaEventRecord(e1, s));
+    BD_TRY(read_scal(h, s));
+    prof_collect(h);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (info) {
+        info->status = status;
+        info->iters = it;
+        info->rel_res = nf > 0.0 ? rr / nf : 0.0;
+        info->true_rel_res = nf > 0.0 ? sqrt(h->host_scal[S_TRR]) / nf : 0.0;
+        info->solve_ms = ms;
+    }
+    return status;
+}
+
+}  // namespace bd
+
+using namespace bd;
+
+extern "C" int amg_vcycle(amg_hierarchy *h, const double *r, double *z, int on_device, void *stream)
+{
+    if (!h || !r || !z) return BD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t bytes = sizeof(double) * 2 * (size_t)h->lev[0].N;
+    if (on_device) {
+        BD_TRY(vcycle_device(h, r, z, s));
+        BD_CUDA(cudaStreamSynchronize(s));
+        prof_collect(h);
+        return BD_OK;
+    }
+    BD_TRY(copy_in(h->r.p, r, bytes, 0, s));
+    BD_TRY(vcycle_device(h, h->r.p, h->z.p, s));
+    BD_TRY(copy_out(z, h->z.p, bytes, 0, s));
+    BD_CUDA(cudaStreamSynchronize(s));
+    prof_collect(h);
+    return BD_OK;
+}
+
+extern "C" int amg_profile_enable(amg_hierarchy *h, int enable)
+{
+    if (!h) return BD_EINVAL;
+    prof_collect(h);
+    h->prof = enable ? 1 : 0;
+    h->prof_sum = amg_kernel_profile{};
+    return BD_OK;
+}
+
+extern "C" int amg_profile_read(const amg_hierarchy *h, amg_kernel_profile *out)
+{
+    if (!h || !out) return BD_EINVAL;
+    *out = h->prof_sum;
+    return BD_OK;
+}
+
+extern "C" int amg_solve(amg_hierarchy *h, const double *f, double *x, int on_device,
+                         const solve_options *opts, void *stream, solve_info *info)
+{
+    if (!h || !f || !x) return BD_EINVAL;
+    solve_options o;
+    solve_options_default(&o);
+    if (opts) o = *opts;
+    if (!(o.rtol > 0.0) || o.max_it < 0) return BD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t bytes = sizeof(double) * 2 * (size_t)h->lev[0].N;
+    if (on_device) return pcg_solve_device(h, f, x, o.warm_start, &o, s, info);
+    // host arrays: f and x are staged in device buffers
+    DBuf<double> fdev;
+    BD_TRY(fdev.alloc(2 * (size_t)h->lev[0].N));
+    BD_TRY(copy_in(fdev.p, f, bytes, 0, s));
+    if (o.warm_start) BD_TRY(copy_in(h->x.p, x, bytes, 0, s));
+    int st = pcg_solve_device(h, fdev.p, h->x.p, o.warm_start, &o, s, info);
+    BD_TRY(copy_out(x, h->x.p, bytes, 0, s));
+    BD_CUDA(cudaStreamSynchronize(s));
+    return st;
+}
