@@ -79,7 +79,8 @@ class RmParams(C.Structure):
 
 #: every entry point declared in include/bidomain.h
 EXPORTS = (
-    "bd_strerror", "bd_launch_count", "bd_dot_exact", "amg_options_default", "solve_options_default", "bd_rm_params_default",
+    "bd_strerror", "bd_launch_count", "bd_dot_exact", "bd_dot_exact_noalloc",
+    "amg_options_default", "solve_options_default", "bd_rm_params_default",
     "bd_assemble", "bd_system_info", "bd_system_export", "bd_system_destroy",
     "amg_setup", "amg_setup_from_csr", "amg_num_levels", "amg_level_info", "amg_export_level",
     "amg_vcycle", "amg_solve", "amg_destroy", "amg_profile_enable", "amg_profile_read",
@@ -104,6 +105,7 @@ def lib():
             L.bd_strerror.restype = C.c_char_p
             L.bd_strerror.argtypes = [C.c_int]
             L.bd_dot_exact.argtypes = [_vp, _vp, C.c_longlong, C.c_int, _P(C.c_double), _vp]
+            L.bd_dot_exact_noalloc.argtypes = [_vp, _vp, C.c_longlong, _vp, _vp]
             L.bd_launch_count.argtypes = []
             L.bd_launch_count.restype = C.c_longlong
             L.amg_options_default.argtypes = [_P(AmgOptions)]
@@ -244,6 +246,21 @@ def bd_dot_exact(x, y, stream=None) -> float:
     out = C.c_double()
     _check(lib().bd_dot_exact(px, py, n, dx, C.byref(out), _stream(stream)), "bd_dot_exact")
     return out.value
+
+
+def bd_dot_exact_noalloc(x, y, out, stream=None):
+    """Allocation-free reproducible dot of two CUDA tensors into the one-element
+    CUDA tensor `out` (stream-ordered, no synchronisation)."""
+    px, dx, kx = _arr(x, np.float64)
+    py, dy, ky = _arr(y, np.float64)
+    po, do, ko = _arr(out, np.float64)
+    if not (dx and dy and do):
+        raise ValueError("x, y and out must be CUDA tensors")
+    if kx.numel() != ky.numel():
+        raise ValueError("x and y must have the same length")
+    _check(lib().bd_dot_exact_noalloc(px, py, kx.numel(), po, _stream(stream)),
+           "bd_dot_exact_noalloc")
+    return out
 
 
 # ------------------------------------------------------------------ a0

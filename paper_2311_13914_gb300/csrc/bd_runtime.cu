@@ -4,6 +4,7 @@
 #include <atomic>
 #include <climits>
 #include <cstring>
+#include <mutex>
 
 #include "bd_common.cuh"
 
@@ -442,6 +443,34 @@ int bsr_to_scalar_csr_host(const BSR &a, int *rp, int *ci, double *v, cudaStream
     return BD_OK;
 }
 
+// ------------------------------------------------------------------ allocation-free dot
+// Scratch of bd_dot_exact_noalloc: one long accumulator (kExactLimbs limbs and
+// a flags word, 552 bytes) in device memory that every GPU loading the library
+// holds until the process exits.  Host code must not use the array's name as a
+// device address: the address is looked up once per device below.
+static __device__ __align__(256) long long g_noalloc_dot_acc[kExactLimbs + 1];
+
+constexpr int kNoallocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static long long *g_noalloc_acc[kNoallocMaxDevices];
+
+// Device address of g_noalloc_dot_acc for the current device (first use on a
+// device performs the lookup).
+static int noalloc_scratch(long long **out)
+{
+    int dev = 0;
+    BD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoallocMaxDevices) return BD_ERANGE;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_acc[dev]) {
+        void *p = nullptr;
+        BD_CUDA(cudaGetSymbolAddress(&p, g_noalloc_dot_acc));
+        g_noalloc_acc[dev] = (long long *)p;
+    }
+    *out = g_noalloc_acc[dev];
+    return BD_OK;
+}
+
 }  // namespace bd
 
 // ------------------------------------------------------------------ public: misc
@@ -487,6 +516,18 @@ extern "C" int bd_dot_exact(const double *x, const double *y, long long n, int o
     BD_CUDA(cudaMemcpyAsync(out, res.p, sizeof(double), cudaMemcpyDeviceToHost, s));
     BD_CUDA(cudaStreamSynchronize(s));
     return BD_OK;
+}
+
+extern "C" int bd_dot_exact_noalloc(const double *x, const double *y, long long n, double *out,
+                                    void *stream)
+{
+    if (!x || !y || !out || n < 0) return BD_EINVAL;
+    if (n > 2147483647LL) return BD_ERANGE;
+    long long *acc = nullptr;
+    BD_TRY(bd::noalloc_scratch(&acc));
+    // exact_dot clears the accumulator on `stream`, then launches the partial
+    // and rounding kernels; nothing is allocated.
+    return bd::exact_dot(x, y, (int)n, out, acc, (cudaStream_t)stream);
 }
 
 extern "C" void amg_options_default(amg_options *o)
