@@ -66,7 +66,8 @@ typedef struct {
     double sil, sit, sel, set;
 } bd_params;
 
-/* Options of the hierarchy (Appendix A defaults from amg_options_default). */
+/* Options of the hierarchy (amg_options_default: the Appendix A values, except that
+ * the graph is squared on every level, not on the first one only). */
 typedef struct {
     double theta;          /* strength threshold, Section 4 (0.06)                  */
     int coarse_eq_limit;   /* stop coarsening at <= this many unknowns (100)        */

@@ -294,7 +294,7 @@ def chebyshev(A, f, x0, degree: int, lo: float, hi: float, x_is_zero: bool = Fal
 
 
 DEFAULT_OPTS = dict(theta=0.06, coarse_eq_limit=100, max_levels=10, cheb_degree=2,
-                    esteig_steps=10, eig_lo=0.05, eig_hi=1.05, seed=0, square_levels=1)
+                    esteig_steps=10, eig_lo=0.05, eig_hi=1.05, seed=0, square_levels=16)
 
 RM_PARAMS = dict(G=1.5, vth=13.0, vp=100.0, eta1=4.4, eta2=0.012, eta3=1.0)
 

@@ -91,7 +91,7 @@ typedef struct {
     int esteig_steps;      /* (10) */
     double eig_lo, eig_hi; /* Chebyshev interval factors (0.05, 1.05) */
     uint64_t seed;
-    int square_levels;     /* levels whose MIS runs on the squared graph (1) */
+    int square_levels;     /* levels whose MIS runs on the squared graph */
 } oc_amg_opts;
 
 typedef struct oc_hier oc_hier;

@@ -538,7 +538,7 @@ extern "C" void amg_options_default(amg_options *o)
     o->max_levels = 10;
     o->cheb_degree = 2;
     o->esteig_steps = 10;
-    o->square_levels = 1;
+    o->square_levels = 16;  /* every level (App. A squares the first only) */
     o->eig_lo = 0.05;
     o->eig_hi = 1.05;
     o->seed = 0;
