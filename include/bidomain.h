@@ -77,6 +77,9 @@ typedef struct {
     int square_levels;     /* levels whose MIS runs on the squared graph (1)        */
     double eig_lo, eig_hi; /* Chebyshev interval [eig_lo, eig_hi]*lambda (0.05,1.05) */
     unsigned long long seed; /* MIS priorities and Lanczos start vector (0)         */
+    int precision;         /* 0: FP64 V-cycle; 1: FP32 V-cycle (values and vectors
+                              of every level in FP32, coarsest solve in FP64) inside
+                              an FP64 flexible CG (Polak-Ribiere beta) (0)          */
 } amg_options;
 
 typedef struct {
@@ -209,8 +212,8 @@ void amg_destroy(amg_hierarchy *h);
 
 /* ---- live timing of the dominant kernel ------------------------------------
  * When enabled, every application of the finest-level operator (the fused
- * SpMV launches of the V-cycle and of PCG) is bracketed by CUDA events on the
- * launching stream; the durations, the algorithmic bytes (matrix values and
+ * SpMV launches of the V-cycle, and of PCG when the V-cycle is FP64) is
+ * bracketed by CUDA events on the launching stream; the durations, the algorithmic bytes (matrix values and
  * indices once, each vector stream once) and the flops (2 per scalar nonzero)
  * are summed.  Enabling resets the sums; reading requires no pending work. */
 typedef struct {
@@ -218,6 +221,7 @@ typedef struct {
     double total_ms;
     double bytes;
     double flops;
+    int precision;     /* 0: the timed launches are FP64, 1: FP32 (V-cycle) */
 } amg_kernel_profile;
 int amg_profile_enable(amg_hierarchy *h, int enable);
 int amg_profile_read(const amg_hierarchy *h, amg_kernel_profile *out);

@@ -50,7 +50,8 @@ class Params(C.Structure):
 class AmgOptions(C.Structure):
     _fields_ = [("theta", C.c_double), ("coarse_eq_limit", C.c_int), ("max_levels", C.c_int),
                 ("cheb_degree", C.c_int), ("esteig_steps", C.c_int), ("square_levels", C.c_int),
-                ("eig_lo", C.c_double), ("eig_hi", C.c_double), ("seed", C.c_ulonglong)]
+                ("eig_lo", C.c_double), ("eig_hi", C.c_double), ("seed", C.c_ulonglong),
+                ("precision", C.c_int)]
 
 
 class SolveOptions(C.Structure):
@@ -69,7 +70,7 @@ class SolveInfo(C.Structure):
 
 class KernelProfile(C.Structure):
     _fields_ = [("launches", C.c_longlong), ("total_ms", C.c_double), ("bytes", C.c_double),
-                ("flops", C.c_double)]
+                ("flops", C.c_double), ("precision", C.c_int)]
 
 
 class RmParams(C.Structure):

@@ -21,6 +21,9 @@ struct Level {
     BSR P, R;                  // prolongator / restriction (not on the coarsest)
     // solve workspace (double2 per node)
     DBuf<double> f, u, r, d, w;
+    // FP32 V-cycle: value copies and workspace (float2 per node)
+    DBuf<float> A32, P32, R32, invdiag32;
+    DBuf<float> f32, u32, r32, d32, w32;
     // Chebyshev coefficients (host copies)
     double ch_inv_theta = 0, ch_c1 = 0, ch_c2 = 0;
 };
@@ -37,6 +40,7 @@ struct FineSell {
     DBuf<int> col;              // slots * 32
     DBuf<double> kk;            // slots * 32 * 2: (Ki, Ke)
     DBuf<double> cm;            // c M_p per node
+    DBuf<float> kk32, cm32;     // FP32 copies for the FP32 V-cycle
 };
 
 }  // namespace bd
@@ -44,6 +48,7 @@ struct FineSell {
 struct amg_hierarchy {
     amg_options opts{};
     int nlev = 0;
+    bool prec32 = false;        // V-cycle in FP32 inside an FP64 flexible CG
     bd::FineSell sell;
     bd::Level lev[bd::kMaxLevels];
     // coarsest level: dense inverse of A_c + s z z^T / z^T z, null vector z
@@ -51,8 +56,8 @@ struct amg_hierarchy {
     bd::DBuf<double> cinv, zc;
     double zz = 0.0;
     // PCG workspace on the finest level
-    bd::DBuf<double> x, r, z, p, q, fp;
-    bd::DBuf<double> partial;   // kRedBlocks x 4
+    bd::DBuf<double> x, r, z, p, q, fp, zold;
+    bd::DBuf<double> partial;   // kRedBlocks x 4 partial sums
     bd::DBuf<double> scal;      // device scalars of the PCG recurrences
     double *host_scal = nullptr;  // pinned mirror
     bd::DBuf<long long> exact_acc;

@@ -1207,7 +1207,6 @@ static int setup_from_level0(amg_hierarchy *h, cudaStream_t s)
     }
     h->nlev = l + 1;
     BD_TRY(build_coarsest(h, l, s));
-    BD_TRY(prepare_solve(h));
     return BD_OK;
 }
 
@@ -1216,7 +1215,7 @@ static int check_opts(const amg_options *o)
     if (!(o->theta >= 0.0) || o->coarse_eq_limit < 2 || o->max_levels < 1 ||
         o->max_levels > kMaxLevels || (o->cheb_degree != 1 && o->cheb_degree != 2) ||
         o->esteig_steps < 1 || o->esteig_steps > 64 || o->square_levels < 0 ||
-        !(o->eig_lo > 0.0) || !(o->eig_hi > o->eig_lo))
+        !(o->eig_lo > 0.0) || !(o->eig_hi > o->eig_lo) || (o->precision != 0 && o->precision != 1))
         return BD_EINVAL;
     return BD_OK;
 }
@@ -1254,7 +1253,9 @@ extern "C" int amg_setup(const bd_system *sys, const amg_options *opts, void *st
         delete h;
         return BD_ECUDA;
     }
-    if ((st = setup_from_level0(h, s)) || (st = build_fine_sell(h, sys, s))) {
+    h->prec32 = o.precision == 1;
+    if ((st = setup_from_level0(h, s)) || (st = build_fine_sell(h, sys, s)) ||
+        (st = prepare_solve(h))) {
         delete h;
         return st;
     }
@@ -1293,9 +1294,11 @@ extern "C" int amg_setup_from_csr(int n, const int *row_ptr, const int *col, con
     amg_hierarchy *h = new (std::nothrow) amg_hierarchy();
     if (!h) return BD_ENOMEM;
     h->opts = o;
+    h->prec32 = o.precision == 1;
     h->lev[0].N = n / 2;
     int st = bsr_from_scalar_csr(n, prp, pci, pv, h->lev[0].A, s);
     if (!st) st = setup_from_level0(h, s);
+    if (!st) st = prepare_solve(h);
     if (st) {
         delete h;
         return st;

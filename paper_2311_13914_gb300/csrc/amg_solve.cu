@@ -1,11 +1,15 @@
 // amg_solve.cu -- a10/a11: V-cycle (Algorithm 2) with Chebyshev-Jacobi
 // smoothing (Appendix A) and the projected PCG of Section 2.2 on the device.
 //
-// Every operator application is one pass of a 2x2-block SpMV kernel whose
-// epilogue fuses the vector work of the step around it (Chebyshev recurrence,
-// residual, correction), so each level streams its matrix four times per
-// cycle and its vectors a few times.  Reductions are deterministic: fixed
-// grid, per-block partial sums, one finishing block.
+// Every operator application is one pass of an SpMV kernel whose epilogue
+// fuses the vector work of the step around it (Chebyshev recurrence, residual,
+// correction), so each level streams its matrix four times per cycle and its
+// vectors a few times.  The V-cycle is written once over the storage scalar S:
+// S = double is the plain FP64 form; S = float keeps FP32 copies of every
+// level's values and vectors (half the bytes, none of the FP64 pipe) and runs
+// inside an FP64 flexible CG, with the coarsest solve, the outer residual, the
+// dot products and the null-space projection in FP64.  Reductions are
+// deterministic: fixed grid, per-block partial sums, one finishing block.
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -14,30 +18,55 @@
 
 namespace bd {
 
-// ------------------------------------------------------------------ SpMV core
-// T lanes cooperate on one 2x2 block row; the block values are read as two
-// 16-byte loads, x as one 16-byte load per block.
-template <int T, class G, class E>
+// ------------------------------------------------------------------ scalar traits
+template <class S> struct V2;
+template <> struct V2<double> {
+    using T = double2;
+    static __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+};
+template <> struct V2<float> {
+    using T = float2;
+    static __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+};
+template <class S> using v2 = typename V2<S>::T;
+
+template <class S> struct BlkS {
+    S a00, a01, a10, a11;
+};
+__device__ __forceinline__ BlkS<double> load_blk(const double *__restrict__ v, size_t t)
+{
+    const double2 p = ((const double2 *)v)[2 * t], q = ((const double2 *)v)[2 * t + 1];
+    return {p.x, p.y, q.x, q.y};
+}
+__device__ __forceinline__ BlkS<float> load_blk(const float *__restrict__ v, size_t t)
+{
+    const float4 p = ((const float4 *)v)[t];
+    return {p.x, p.y, p.z, p.w};
+}
+
+// ------------------------------------------------------------------ block-CSR SpMV
+// T lanes cooperate on one 2x2 block row (T = 1: one thread per row, no
+// reduction).  The row loop is warp-uniform so every lane reaches the shuffles.
+template <int T, class S, class G, class E>
 __global__ void __launch_bounds__(256) k_bsr(int N, const int *__restrict__ rp,
-                                              const int *__restrict__ ci,
-                                              const double2 *__restrict__ v, G gather, E epi)
+                                              const int *__restrict__ ci, const S *__restrict__ v,
+                                              G gather, E epi)
 {
     const int lane = threadIdx.x & (T - 1);
     const int groups = (gridDim.x * blockDim.x) / T;
-    // warp-uniform row loop: every lane reaches the shuffles below
     const int warp_first = ((blockIdx.x * blockDim.x + threadIdx.x) & ~31) / T;
     const int g_in_warp = (threadIdx.x & 31) / T;
     for (int pw = warp_first; pw < N; pw += groups) {
         const int p = pw + g_in_warp;
         const bool act = p < N;
-        double y0 = 0.0, y1 = 0.0;
+        S y0 = 0, y1 = 0;
         const int e = act ? rp[p + 1] : 0;
         for (int t = act ? rp[p] + lane : 0; t < e; t += T) {
             const int q = ci[t];
-            const double2 a01 = v[2 * (size_t)t], a23 = v[2 * (size_t)t + 1];
-            const double2 x = gather(q);
-            y0 = fma(a01.x, x.x, fma(a01.y, x.y, y0));
-            y1 = fma(a23.x, x.x, fma(a23.y, x.y, y1));
+            const BlkS<S> a = load_blk(v, (size_t)t);
+            const v2<S> x = gather(q);
+            y0 = fma(a.a00, x.x, fma(a.a01, x.y, y0));
+            y1 = fma(a.a10, x.x, fma(a.a11, x.y, y1));
         }
 #pragma unroll
         for (int o = T / 2; o > 0; o >>= 1) {
@@ -48,157 +77,195 @@ __global__ void __launch_bounds__(256) k_bsr(int N, const int *__restrict__ rp,
     }
 }
 
-struct GatherVec {
-    const double2 *__restrict__ x;
-    __device__ __forceinline__ double2 operator()(int q) const { return x[q]; }
+// ------------------------------------------------------------------ finest level, sliced ELL
+// One thread per row; slot j of slice s holds entry j of its 32 rows
+// contiguously, so every slot is one coalesced (Ki, Ke) load and one 128-byte
+// column load per warp.  Per node pair: s = v_q + u_q, a += Ki s, b += Ke u_q;
+// then y_v = c M_p v_p + a, y_u = a + b.
+template <class S, class G, class E>
+__global__ void __launch_bounds__(256) k_sell(int N, const int *__restrict__ sptr,
+                                               const int *__restrict__ col,
+                                               const v2<S> *__restrict__ kk,
+                                               const S *__restrict__ cm, G gather, E epi)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
+        const int sl = p >> 5, lane = p & 31;
+        const int j1 = sptr[sl + 1];
+        S a = 0, b = 0;
+        for (int j = sptr[sl]; j < j1; j++) {
+            const size_t idx = (size_t)j * 32 + lane;
+            const int q = col[idx];
+            const v2<S> k = kk[idx];
+            const v2<S> x = gather(q);
+            a = fma(k.x, x.x + x.y, a);
+            b = fma(k.y, x.y, b);
+        }
+        const v2<S> xp = gather(p);
+        epi(p, fma(cm[p], xp.x, a), a + b);
+    }
+}
+
+// ------------------------------------------------------------------ fused epilogues
+template <class S> struct GatherVec {
+    const v2<S> *__restrict__ x;
+    __device__ __forceinline__ v2<S> operator()(int q) const { return x[q]; }
 };
 
 // pre-smoothing, degree 2 from zero, d0 = D^{-1} f / theta precomputed:
 // x1 = d0, r1 = f - A d0, d1 = c1 d0 + c2 D^{-1} r1, u = x1 + d1
-struct EpiPre {
-    const double2 *__restrict__ f;
-    const double2 *__restrict__ invd;
-    const double2 *__restrict__ d0;
-    double2 *__restrict__ u;
-    double c1, c2;
-    __device__ __forceinline__ void operator()(int p, double y0, double y1) const {
-        double2 fp = f[p], id = invd[p], dp = d0[p];
-        double r0 = fp.x - y0, r1 = fp.y - y1;
-        u[p] = make_double2(dp.x + (c1 * dp.x + c2 * id.x * r0), dp.y + (c1 * dp.y + c2 * id.y * r1));
+template <class S> struct EpiPre {
+    const v2<S> *__restrict__ f;
+    const v2<S> *__restrict__ invd;
+    const v2<S> *__restrict__ d0;
+    v2<S> *__restrict__ u;
+    S c1, c2;
+    __device__ __forceinline__ void operator()(int p, S y0, S y1) const {
+        const v2<S> fp = f[p], id = invd[p], dp = d0[p];
+        const S r0 = fp.x - y0, r1 = fp.y - y1;
+        u[p] = V2<S>::mk(dp.x + (c1 * dp.x + c2 * id.x * r0), dp.y + (c1 * dp.y + c2 * id.y * r1));
     }
 };
 
 // restriction output f_c = R r together with d0_c = D_c^{-1} f_c / theta_c
-struct EpiStoreD0 {
-    double2 *__restrict__ f;
-    double2 *__restrict__ d0;
-    const double2 *__restrict__ invd;
-    double it;
-    __device__ __forceinline__ void operator()(int p, double y0, double y1) const {
-        f[p] = make_double2(y0, y1);
-        double2 id = invd[p];
-        d0[p] = make_double2(y0 * id.x * it, y1 * id.y * it);
+template <class S> struct EpiStoreD0 {
+    v2<S> *__restrict__ f;
+    v2<S> *__restrict__ d0;
+    const v2<S> *__restrict__ invd;
+    S it;
+    __device__ __forceinline__ void operator()(int p, S y0, S y1) const {
+        f[p] = V2<S>::mk(y0, y1);
+        const v2<S> id = invd[p];
+        d0[p] = V2<S>::mk(y0 * id.x * it, y1 * id.y * it);
     }
 };
 
-struct EpiResid {  // r = f - A u
-    const double2 *__restrict__ f;
-    double2 *__restrict__ r;
-    __device__ __forceinline__ void operator()(int p, double y0, double y1) const {
-        double2 fp = f[p];
-        r[p] = make_double2(fp.x - y0, fp.y - y1);
+template <class S> struct EpiResid {  // r = f - A u
+    const v2<S> *__restrict__ f;
+    v2<S> *__restrict__ r;
+    __device__ __forceinline__ void operator()(int p, S y0, S y1) const {
+        const v2<S> fp = f[p];
+        r[p] = V2<S>::mk(fp.x - y0, fp.y - y1);
     }
 };
 
-struct EpiStore {
-    double2 *__restrict__ y;
-    __device__ __forceinline__ void operator()(int p, double y0, double y1) const {
-        y[p] = make_double2(y0, y1);
-    }
-};
-
-struct EpiAdd {  // u += P e_c
-    double2 *__restrict__ u;
-    __device__ __forceinline__ void operator()(int p, double y0, double y1) const {
-        double2 a = u[p];
-        u[p] = make_double2(a.x + y0, a.y + y1);
+template <class S> struct EpiAdd {  // u += P e_c
+    v2<S> *__restrict__ u;
+    __device__ __forceinline__ void operator()(int p, S y0, S y1) const {
+        const v2<S> a = u[p];
+        u[p] = V2<S>::mk(a.x + y0, a.y + y1);
     }
 };
 
 // post-smoothing, first half: r0 = f - A u, d0 = D^{-1} r0 / theta, w = u + d0
-struct EpiPost1 {
-    const double2 *__restrict__ f;
-    const double2 *__restrict__ invd;
-    const double2 *__restrict__ u;
-    double2 *__restrict__ r;
-    double2 *__restrict__ d;
-    double2 *__restrict__ w;
-    double it;
-    __device__ __forceinline__ void operator()(int p, double y0, double y1) const {
-        double2 fp = f[p], id = invd[p], up = u[p];
-        double r0 = fp.x - y0, r1 = fp.y - y1;
-        double d0 = r0 * id.x * it, d1 = r1 * id.y * it;
-        r[p] = make_double2(r0, r1);
-        d[p] = make_double2(d0, d1);
-        w[p] = make_double2(up.x + d0, up.y + d1);
+template <class S> struct EpiPost1 {
+    const v2<S> *__restrict__ f;
+    const v2<S> *__restrict__ invd;
+    const v2<S> *__restrict__ u;
+    v2<S> *__restrict__ r;
+    v2<S> *__restrict__ d;
+    v2<S> *__restrict__ w;
+    S it;
+    __device__ __forceinline__ void operator()(int p, S y0, S y1) const {
+        const v2<S> fp = f[p], id = invd[p], up = u[p];
+        const S r0 = fp.x - y0, r1 = fp.y - y1;
+        const S d0 = r0 * id.x * it, d1 = r1 * id.y * it;
+        r[p] = V2<S>::mk(r0, r1);
+        d[p] = V2<S>::mk(d0, d1);
+        w[p] = V2<S>::mk(up.x + d0, up.y + d1);
     }
 };
 
 // post-smoothing, second half: r1 = r0 - A d0, d1 = c1 d0 + c2 D^{-1} r1, u = w + d1
-struct EpiPost2 {
-    const double2 *__restrict__ r;
-    const double2 *__restrict__ d;
-    const double2 *__restrict__ invd;
-    const double2 *__restrict__ w;
-    double2 *__restrict__ u;
-    double c1, c2;
-    __device__ __forceinline__ void operator()(int p, double y0, double y1) const {
-        double2 rp_ = r[p], dp = d[p], id = invd[p], wp = w[p];
-        double r0 = rp_.x - y0, r1 = rp_.y - y1;
-        u[p] = make_double2(wp.x + (c1 * dp.x + c2 * id.x * r0), wp.y + (c1 * dp.y + c2 * id.y * r1));
+template <class S> struct EpiPost2 {
+    const v2<S> *__restrict__ r;
+    const v2<S> *__restrict__ d;
+    const v2<S> *__restrict__ invd;
+    const v2<S> *__restrict__ w;
+    v2<S> *__restrict__ u;
+    S c1, c2;
+    __device__ __forceinline__ void operator()(int p, S y0, S y1) const {
+        const v2<S> rp_ = r[p], dp = d[p], id = invd[p], wp = w[p];
+        const S r0 = rp_.x - y0, r1 = rp_.y - y1;
+        u[p] = V2<S>::mk(wp.x + (c1 * dp.x + c2 * id.x * r0), wp.y + (c1 * dp.y + c2 * id.y * r1));
     }
 };
 
-template <class G, class E>
-static int launch_bsr(const BSR &A, int T, G g, E e, cudaStream_t s)
+// ------------------------------------------------------------------ per-level views
+// Value and vector pointers of one level in precision S (index arrays are shared).
+template <class S> struct LV {
+    const S *Av, *Pv, *Rv;
+    const v2<S> *invd;
+    v2<S> *f, *u, *r, *d, *w;
+    const v2<S> *kk;  // finest level, sliced ELL
+    const S *cm;
+};
+
+template <class S> static LV<S> view(amg_hierarchy *h, int l);
+template <> LV<double> view<double>(amg_hierarchy *h, int l)
+{
+    Level &L = h->lev[l];
+    LV<double> v;
+    v.Av = L.A.v.p;
+    v.Pv = L.P.v.p;
+    v.Rv = L.R.v.p;
+    v.invd = (const double2 *)L.invdiag.p;
+    v.f = (double2 *)L.f.p;
+    v.u = (double2 *)L.u.p;
+    v.r = (double2 *)L.r.p;
+    v.d = (double2 *)L.d.p;
+    v.w = (double2 *)L.w.p;
+    v.kk = (const double2 *)h->sell.kk.p;
+    v.cm = h->sell.cm.p;
+    return v;
+}
+template <> LV<float> view<float>(amg_hierarchy *h, int l)
+{
+    Level &L = h->lev[l];
+    LV<float> v;
+    v.Av = L.A32.p;
+    v.Pv = L.P32.p;
+    v.Rv = L.R32.p;
+    v.invd = (const float2 *)L.invdiag32.p;
+    v.f = (float2 *)L.f32.p;
+    v.u = (float2 *)L.u32.p;
+    v.r = (float2 *)L.r32.p;
+    v.d = (float2 *)L.d32.p;
+    v.w = (float2 *)L.w32.p;
+    v.kk = (const float2 *)h->sell.kk32.p;
+    v.cm = h->sell.cm32.p;
+    return v;
+}
+
+template <class S, class G, class E>
+static int launch_bsr(const BSR &A, const S *vals, int T, G g, E e, cudaStream_t s)
 {
     int N = A.nbr;
     if (N <= 0) return BD_OK;
     const int threads = 256;
     long long groups_per_block = threads / T;
     int grid = (int)std::min<long long>((N + groups_per_block - 1) / groups_per_block, (long long)kSM * 16);
-    const double2 *v = (const double2 *)A.v.p;
     switch (T) {
-    case 1: k_bsr<1><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, v, g, e); ::bd::note_launch(); break;
-    case 2: k_bsr<2><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, v, g, e); ::bd::note_launch(); break;
-    case 4: k_bsr<4><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, v, g, e); ::bd::note_launch(); break;
-    case 8: k_bsr<8><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, v, g, e); ::bd::note_launch(); break;
-    case 16: k_bsr<16><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, v, g, e); ::bd::note_launch(); break;
-    default: k_bsr<32><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, v, g, e); ::bd::note_launch(); break;
+    case 1: k_bsr<1, S><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, vals, g, e); ::bd::note_launch(); break;
+    case 2: k_bsr<2, S><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, vals, g, e); ::bd::note_launch(); break;
+    case 4: k_bsr<4, S><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, vals, g, e); ::bd::note_launch(); break;
+    case 8: k_bsr<8, S><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, vals, g, e); ::bd::note_launch(); break;
+    case 16: k_bsr<16, S><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, vals, g, e); ::bd::note_launch(); break;
+    default: k_bsr<32, S><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, vals, g, e); ::bd::note_launch(); break;
     }
     BD_LAUNCH_CHECK();
     return BD_OK;
 }
 
-// Lanes per block row.  Every lane-level reduction step costs FP64 adds, which
-// are scarce on this part, so rows are handled by as few lanes as their length
-// allows (one thread per row for short rows); small levels get more lanes per
-// row so that the grid still fills the GPU.
+// Lanes per block row.  Every lane-level reduction step costs adds that are
+// scarce in FP64 on this part, so rows are handled by as few lanes as their
+// length allows (one thread per row for short rows); small levels get more
+// lanes per row so that the grid still fills the GPU.
 static int lanes_for(const BSR &A)
 {
     double avg = A.nbr > 0 ? (double)A.nb / A.nbr : 1.0;
     int T = avg <= 40 ? 1 : (avg <= 160 ? 4 : (avg <= 640 ? 8 : 16));
     while (T < 32 && (long long)A.nbr * T < 65536) T <<= 1;
     return T;
-}
-
-// ------------------------------------------------------------------ finest level, sliced ELL
-// One thread per row; slot j of slice s holds entry j of its 32 rows
-// contiguously, so every slot is one coalesced 512-byte (Ki, Ke) load and one
-// 128-byte column load per warp.  Per node pair: s = v_q + u_q,
-// a += Ki s, b += Ke u_q (three FP64 operations, 20 bytes); then
-// y_v = c M_p v_p + a, y_u = a + b.
-template <class G, class E>
-__global__ void __launch_bounds__(256) k_sell(int N, const int *__restrict__ sptr,
-                                               const int *__restrict__ col,
-                                               const double2 *__restrict__ kk,
-                                               const double *__restrict__ cm, G gather, E epi)
-{
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
-        const int sl = p >> 5, lane = p & 31;
-        const int j1 = sptr[sl + 1];
-        double a = 0.0, b = 0.0;
-        for (int j = sptr[sl]; j < j1; j++) {
-            const size_t idx = (size_t)j * 32 + lane;
-            const int q = col[idx];
-            const double2 k = kk[idx];
-            const double2 x = gather(q);
-            a = fma(k.x, x.x + x.y, a);
-            b = fma(k.y, x.y, b);
-        }
-        const double2 xp = gather(p);
-        epi(p, fma(cm[p], xp.x, a), a + b);
-    }
 }
 
 __global__ void k_sell_width(int N, const int *__restrict__ rp, int *__restrict__ w, int nslices)
@@ -258,20 +325,20 @@ int build_fine_sell(amg_hierarchy *h, const bd_system *sys, cudaStream_t s)
     return BD_OK;
 }
 
-// operator application of level l: sliced ELL on the finest level when
-// available, 2x2-block CSR otherwise
-template <class G, class E>
-static int apply_level(amg_hierarchy *h, int l, G g, E e, cudaStream_t s)
+// operator application of level l in precision S: sliced ELL on the finest
+// level when available, 2x2-block CSR otherwise
+template <class S, class G, class E>
+static int apply_level(amg_hierarchy *h, int l, const LV<S> &lv, G g, E e, cudaStream_t s)
 {
     const Level &L = h->lev[l];
     if (l == 0 && h->sell.valid) {
         const FineSell &F = h->sell;
         int grid = (int)std::min<long long>(((long long)L.N + 255) / 256, (long long)kSM * 8);
-        k_sell<<<grid, 256, 0, s>>>(L.N, F.sptr.p, F.col.p, (const double2 *)F.kk.p, F.cm.p, g, e); ::bd::note_launch();
+        k_sell<S><<<grid, 256, 0, s>>>(L.N, F.sptr.p, F.col.p, lv.kk, lv.cm, g, e); ::bd::note_launch();
         BD_LAUNCH_CHECK();
         return BD_OK;
     }
-    return launch_bsr(L.A, lanes_for(L.A), g, e, s);
+    return launch_bsr<S>(L.A, lv.Av, lanes_for(L.A), g, e, s);
 }
 
 // ------------------------------------------------------------------ live kernel timing
@@ -316,28 +383,33 @@ void prof_collect(amg_hierarchy *h)
     h->ev_used = 0;
 }
 
-// Algorithmic bytes of one finest-level operator application: the stored
-// matrix once (sliced ELL: 20 bytes per slot incl. padding, plus slice offsets
-// and c M; block CSR: 36 bytes per block plus row offsets) and `vec16` 16-byte
-// per-node vector streams.  Flops: 2 per scalar nonzero (8 per 2x2 block).
-static double fine_bytes(const amg_hierarchy *h, const Level &L, int vec16)
+// Algorithmic bytes of one finest-level operator application in precision S:
+// the stored matrix once (sliced ELL: Ki, Ke and a column per slot incl.
+// padding, slice offsets, c M; block CSR: four values and a column per block,
+// row offsets) and `vec` per-node vector streams of two S each.
+// Flops: 2 per scalar nonzero (8 per 2x2 block).
+template <class S>
+static double fine_bytes(const amg_hierarchy *h, const Level &L, int vec)
 {
-    double mat = h->sell.valid
-                     ? 20.0 * 32.0 * (double)h->sell.slots + 4.0 * (h->sell.nslices + 1) + 8.0 * L.N
-                     : 36.0 * (double)L.A.nb + 4.0 * (L.N + 1);
-    return mat + 16.0 * vec16 * (double)L.N;
+    const double sz = (double)sizeof(S);
+    double mat = h->sell.valid ? (2 * sz + 4.0) * 32.0 * (double)h->sell.slots +
+                                     4.0 * (h->sell.nslices + 1) + sz * L.N
+                               : (4 * sz + 4.0) * (double)L.A.nb + 4.0 * (L.N + 1);
+    return mat + 2 * sz * vec * (double)L.N;
 }
-static double fine_flops(const amg_hierarchy *, const Level &L) { return 8.0 * (double)L.A.nb; }
+static double fine_flops(const Level &L) { return 8.0 * (double)L.A.nb; }
 
 // ------------------------------------------------------------------ coarsest level
-// x = Cinv (r - (z.r / z.z) z); one block, one warp per output row.
+// x = Cinv (r - (z.r / z.z) z) in FP64 whatever the storage precision; one
+// block, one warp per output row.
+template <class S>
 __global__ void k_coarse_solve(int n, const double *__restrict__ cinv, const double *__restrict__ z,
-                               double zz, const double *__restrict__ r, double *__restrict__ x)
+                               double zz, const S *__restrict__ r, S *__restrict__ x)
 {
     extern __shared__ double rs[];
     __shared__ double red[32];
     double part = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) part += z[i] * r[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) part += z[i] * (double)r[i];
     for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
     __syncthreads();
@@ -348,7 +420,7 @@ __global__ void k_coarse_solve(int n, const double *__restrict__ cinv, const dou
     }
     __syncthreads();
     double a = zz > 0.0 ? red[0] / zz : 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) rs[i] = r[i] - a * z[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) rs[i] = (double)r[i] - a * z[i];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = warp; i < n; i += nw) {
@@ -356,110 +428,162 @@ __global__ void k_coarse_solve(int n, const double *__restrict__ cinv, const dou
         double sacc = 0.0;
         for (int j = lane; j < n; j += 32) sacc += row[j] * rs[j];
         for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-        if (lane == 0) x[i] = sacc;
+        if (lane == 0) x[i] = (S)sacc;
     }
 }
 
-__global__ void k_copy2(int N, const double2 *__restrict__ a, double2 *__restrict__ b)
+template <class S>
+__global__ void k_copy2(int N, const v2<S> *__restrict__ a, v2<S> *__restrict__ b)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) b[i] = a[i];
 }
 
-__global__ void k_scale_d0(int N, const double2 *__restrict__ f, const double2 *__restrict__ invd,
-                           double it, double2 *__restrict__ u)
+template <class S>
+__global__ void k_scale_d0(int N, const v2<S> *__restrict__ f, const v2<S> *__restrict__ invd, S it,
+                           v2<S> *__restrict__ d0)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        double2 a = f[i], b = invd[i];
-        u[i] = make_double2(a.x * b.x * it, a.y * b.y * it);
+        const v2<S> a = f[i], b = invd[i];
+        d0[i] = V2<S>::mk(a.x * b.x * it, a.y * b.y * it);
     }
 }
 
-int vcycle_device(amg_hierarchy *h, const double *r_dev, double *z_dev, cudaStream_t s)
+// FP64 residual in, FP32 right-hand side and d0 of the finest level out
+__global__ void k_in32(int N, const double2 *__restrict__ r, const float2 *__restrict__ invd, float it,
+                       float2 *__restrict__ f, float2 *__restrict__ d0)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const double2 a = r[i];
+        const float2 b = invd[i];
+        const float f0 = (float)a.x, f1 = (float)a.y;
+        f[i] = make_float2(f0, f1);
+        d0[i] = make_float2(f0 * b.x * it, f1 * b.y * it);
+    }
+}
+
+__global__ void k_out64(int N, const float2 *__restrict__ u, double2 *__restrict__ z)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const float2 a = u[i];
+        z[i] = make_double2((double)a.x, (double)a.y);
+    }
+}
+
+__global__ void k_to_f32(long long n, const double *__restrict__ a, float *__restrict__ b)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+// One V-cycle in precision S; f0/u0 are the finest level's right-hand side and
+// output (d0 of the finest level must already be in lev[0]'s d vector).
+template <class S>
+static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_t s)
 {
     const int nl = h->nlev;
     const bool deg2 = h->opts.cheb_degree == 2;
     for (int l = 0; l < nl - 1; l++) {
         Level &L = h->lev[l];
-        const double2 *f = (const double2 *)(l == 0 ? r_dev : L.f.p);
-        double2 *u = (double2 *)(l == 0 ? z_dev : L.u.p);
-        const double2 *invd = (const double2 *)L.invdiag.p;
-        double2 *d0 = (double2 *)L.d.p;
-        if (l == 0) {  // coarser levels receive d0 from the restriction epilogue
-            k_scale_d0<<<grid_for(L.N, 256), 256, 0, s>>>(L.N, f, invd, L.ch_inv_theta, d0); ::bd::note_launch();
-            BD_LAUNCH_CHECK();
-        }
+        const LV<S> lv = view<S>(h, l);
+        const v2<S> *f = l == 0 ? f0 : lv.f;
+        v2<S> *u = l == 0 ? u0 : lv.u;
+        v2<S> *d0 = lv.d;
         if (deg2) {
             int sl = l == 0 ? prof_begin(h, s) : -1;
-            BD_TRY(apply_level(h, l, GatherVec{d0}, EpiPre{f, invd, d0, u, L.ch_c1, L.ch_c2}, s));
-            prof_end(h, sl, fine_bytes(h, L, 4), fine_flops(h, L), s);
+            BD_TRY(apply_level<S>(h, l, lv, GatherVec<S>{d0},
+                                  EpiPre<S>{f, lv.invd, d0, u, (S)L.ch_c1, (S)L.ch_c2}, s));
+            prof_end(h, sl, fine_bytes<S>(h, L, 4), fine_flops(L), s);
         } else {
-            k_copy2<<<grid_for(L.N, 256), 256, 0, s>>>(L.N, d0, u); ::bd::note_launch();
+            k_copy2<S><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, d0, u); ::bd::note_launch();
             BD_LAUNCH_CHECK();
         }
         int sr = l == 0 ? prof_begin(h, s) : -1;
-        BD_TRY(apply_level(h, l, GatherVec{u}, EpiResid{f, (double2 *)L.r.p}, s));
-        prof_end(h, sr, fine_bytes(h, L, 3), fine_flops(h, L), s);
-        Level &C = h->lev[l + 1];
-        BD_TRY(launch_bsr(L.R, lanes_for(L.R), GatherVec{(const double2 *)L.r.p},
-                          EpiStoreD0{(double2 *)C.f.p, (double2 *)C.d.p,
-                                     (const double2 *)C.invdiag.p, C.ch_inv_theta},
-                          s));
+        BD_TRY(apply_level<S>(h, l, lv, GatherVec<S>{u}, EpiResid<S>{f, lv.r}, s));
+        prof_end(h, sr, fine_bytes<S>(h, L, 3), fine_flops(L), s);
+        const Level &C = h->lev[l + 1];
+        const LV<S> cv = view<S>(h, l + 1);
+        BD_TRY(launch_bsr<S>(L.R, lv.Rv, lanes_for(L.R), GatherVec<S>{lv.r},
+                             EpiStoreD0<S>{cv.f, cv.d, cv.invd, (S)C.ch_inv_theta}, s));
     }
     {
-        Level &C = h->lev[nl - 1];
-        const double *f = nl == 1 ? r_dev : C.f.p;
-        double *u = nl == 1 ? z_dev : C.u.p;
+        const LV<S> cv = view<S>(h, nl - 1);
+        const S *f = (const S *)(nl == 1 ? f0 : cv.f);
+        S *u = (S *)(nl == 1 ? u0 : cv.u);
         size_t smem = sizeof(double) * (size_t)h->nc;
-        k_coarse_solve<<<1, 1024, smem, s>>>(h->nc, h->cinv.p, h->zc.p, h->zz, f, u); ::bd::note_launch();
+        k_coarse_solve<S><<<1, 1024, smem, s>>>(h->nc, h->cinv.p, h->zc.p, h->zz, f, u); ::bd::note_launch();
         BD_LAUNCH_CHECK();
     }
     for (int l = nl - 2; l >= 0; l--) {
         Level &L = h->lev[l];
-        const double2 *f = (const double2 *)(l == 0 ? r_dev : L.f.p);
-        double2 *u = (double2 *)(l == 0 ? z_dev : L.u.p);
-        const double2 *invd = (const double2 *)L.invdiag.p;
-        BD_TRY(launch_bsr(L.P, lanes_for(L.P), GatherVec{(const double2 *)h->lev[l + 1].u.p}, EpiAdd{u}, s));
+        const LV<S> lv = view<S>(h, l);
+        const v2<S> *f = l == 0 ? f0 : lv.f;
+        v2<S> *u = l == 0 ? u0 : lv.u;
+        const LV<S> cv = view<S>(h, l + 1);
+        BD_TRY(launch_bsr<S>(L.P, lv.Pv, lanes_for(L.P), GatherVec<S>{cv.u}, EpiAdd<S>{u}, s));
         int s1 = l == 0 ? prof_begin(h, s) : -1;
-        BD_TRY(apply_level(h, l, GatherVec{u},
-                           EpiPost1{f, invd, u, (double2 *)L.r.p, (double2 *)L.d.p, (double2 *)L.w.p,
-                                    L.ch_inv_theta},
-                           s));
-        prof_end(h, s1, fine_bytes(h, L, 6), fine_flops(h, L), s);
+        BD_TRY(apply_level<S>(h, l, lv, GatherVec<S>{u},
+                              EpiPost1<S>{f, lv.invd, u, lv.r, lv.d, lv.w, (S)L.ch_inv_theta}, s));
+        prof_end(h, s1, fine_bytes<S>(h, L, 6), fine_flops(L), s);
         if (deg2) {
             int s2 = l == 0 ? prof_begin(h, s) : -1;
-            BD_TRY(apply_level(h, l, GatherVec{(const double2 *)L.d.p},
-                               EpiPost2{(const double2 *)L.r.p, (const double2 *)L.d.p, invd,
-                                        (const double2 *)L.w.p, u, L.ch_c1, L.ch_c2},
-                               s));
-            prof_end(h, s2, fine_bytes(h, L, 5), fine_flops(h, L), s);
+            BD_TRY(apply_level<S>(h, l, lv, GatherVec<S>{lv.d},
+                                  EpiPost2<S>{lv.r, lv.d, lv.invd, lv.w, u, (S)L.ch_c1, (S)L.ch_c2}, s));
+            prof_end(h, s2, fine_bytes<S>(h, L, 5), fine_flops(L), s);
         } else {
-            k_copy2<<<grid_for(L.N, 256), 256, 0, s>>>(L.N, (const double2 *)L.w.p, u); ::bd::note_launch();
+            k_copy2<S><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, lv.w, u); ::bd::note_launch();
             BD_LAUNCH_CHECK();
         }
     }
     return BD_OK;
 }
 
+// z = B r with FP64 vectors at the boundary, in the hierarchy's precision.
+int vcycle_device(amg_hierarchy *h, const double *r_dev, double *z_dev, cudaStream_t s)
+{
+    Level &L0 = h->lev[0];
+    if (h->prec32) {
+        const LV<float> v0 = view<float>(h, 0);
+        k_in32<<<grid_for(L0.N, 256), 256, 0, s>>>(L0.N, (const double2 *)r_dev, v0.invd,
+                                                   (float)L0.ch_inv_theta, v0.f, v0.d); ::bd::note_launch();
+        BD_LAUNCH_CHECK();
+        BD_TRY(vcycle_impl<float>(h, v0.f, v0.u, s));
+        k_out64<<<grid_for(L0.N, 256), 256, 0, s>>>(L0.N, v0.u, (double2 *)z_dev); ::bd::note_launch();
+        BD_LAUNCH_CHECK();
+        return BD_OK;
+    }
+    const LV<double> v0 = view<double>(h, 0);
+    if (h->nlev > 1) {
+        k_scale_d0<double><<<grid_for(L0.N, 256), 256, 0, s>>>(L0.N, (const double2 *)r_dev, v0.invd,
+                                                               L0.ch_inv_theta, v0.d); ::bd::note_launch();
+        BD_LAUNCH_CHECK();
+    }
+    return vcycle_impl<double>(h, (const double2 *)r_dev, (double2 *)z_dev, s);
+}
+
 // ------------------------------------------------------------------ PCG reductions
 // scal[] slots of the device scalars
 enum {
-    S_SUMFU = 0, S_FF, S_NF2, S_RR, S_RZ, S_RZOLD, S_PQ, S_ALPHA, S_BETA, S_MEANZ,
-    S_SUMRU, S_BREAK, S_MEANF, S_TRR, S_MEANX, S_NSLOTS
+    S_SUMFU = 0, S_FF, S_NF2, S_RR, S_RZ, S_PQ, S_ALPHA, S_BETA, S_MEANZ,
+    S_BREAK, S_MEANF, S_TRR, S_MEANX, S_NSLOTS
 };
+constexpr int kPart = 4;  // partial sums per block
 
-__device__ __forceinline__ void block_partials(double a, double b, double c, double *partial)
+__device__ __forceinline__ void block_partials(double a, double b, double c, double d, double *partial)
 {
-    __shared__ double red[3][32];
+    __shared__ double red[kPart][32];
     for (int o = 16; o; o >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
         b += __shfl_xor_sync(0xffffffffu, b, o);
         c += __shfl_xor_sync(0xffffffffu, c, o);
+        d += __shfl_xor_sync(0xffffffffu, d, o);
     }
     int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) {
         red[0][w] = a;
         red[1][w] = b;
         red[2][w] = c;
+        red[3][w] = d;
     }
     __syncthreads();
     if (w == 0) {
@@ -467,48 +591,57 @@ __device__ __forceinline__ void block_partials(double a, double b, double c, dou
         a = l < nw ? red[0][l] : 0.0;
         b = l < nw ? red[1][l] : 0.0;
         c = l < nw ? red[2][l] : 0.0;
+        d = l < nw ? red[3][l] : 0.0;
         for (int o = 16; o; o >>= 1) {
             a += __shfl_xor_sync(0xffffffffu, a, o);
             b += __shfl_xor_sync(0xffffffffu, b, o);
             c += __shfl_xor_sync(0xffffffffu, c, o);
+            d += __shfl_xor_sync(0xffffffffu, d, o);
         }
         if (l == 0) {
-            partial[3 * blockIdx.x + 0] = a;
-            partial[3 * blockIdx.x + 1] = b;
-            partial[3 * blockIdx.x + 2] = c;
+            double *o_ = partial + kPart * blockIdx.x;
+            o_[0] = a;
+            o_[1] = b;
+            o_[2] = c;
+            o_[3] = d;
         }
     }
 }
 
-// Reduce the kRedBlocks partial triples in a fixed order, then apply `stage`.
+// Reduce the per-block partial sums in a fixed order, then apply `stage`.
 __global__ void k_finish(const double *__restrict__ partial, int nparts, double *scal, int stage,
-                         int N, int first)
+                         int N, int first, int flexible)
 {
-    __shared__ double red[3][32];
-    double a = 0.0, b = 0.0, c = 0.0;
+    __shared__ double red[kPart][32];
+    double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-        a += partial[3 * i];
-        b += partial[3 * i + 1];
-        c += partial[3 * i + 2];
+        const double *q = partial + kPart * i;
+        a += q[0];
+        b += q[1];
+        c += q[2];
+        d += q[3];
     }
     for (int o = 16; o; o >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
         b += __shfl_xor_sync(0xffffffffu, b, o);
         c += __shfl_xor_sync(0xffffffffu, c, o);
+        d += __shfl_xor_sync(0xffffffffu, d, o);
     }
     int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) {
         red[0][w] = a;
         red[1][w] = b;
         red[2][w] = c;
+        red[3][w] = d;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
-    a = b = c = 0.0;
+    a = b = c = d = 0.0;
     for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
         a += red[0][i];
         b += red[1][i];
         c += red[2][i];
+        d += red[3][i];
     }
     switch (stage) {
     case 0:  // f statistics: sum f_u, ||f||^2
@@ -522,11 +655,14 @@ __global__ void k_finish(const double *__restrict__ partial, int nparts, double 
     case 2:  // ||r||^2
         scal[S_RR] = a;
         break;
-    case 3: {  // z statistics: sum z_u, sum r_u, r.z
+    case 3: {  // z statistics: sum z_u, sum r_u, r.z, r.z_old
         double mz = a / N;
-        double rz = c - mz * b;
+        double rz = c - mz * b;  // r . (z projected)
         scal[S_MEANZ] = mz;
-        scal[S_BETA] = first ? 0.0 : rz / scal[S_RZ];
+        // standard CG: beta = rz_new / rz_old; flexible (Polak-Ribiere):
+        // beta = (r.z_new - r.z_old) / rz_old with z_old the previous projected z
+        double num = flexible ? rz - d : rz;
+        scal[S_BETA] = first ? 0.0 : num / scal[S_RZ];
         scal[S_RZ] = rz;
         break;
     }
@@ -551,7 +687,7 @@ __global__ void k_f_stats(int N, const double2 *__restrict__ f, double *partial)
         a += v.y;
         b += v.x * v.x + v.y * v.y;
     }
-    block_partials(a, b, 0.0, partial);
+    block_partials(a, b, 0.0, 0.0, partial);
 }
 
 __global__ void k_project_f(int N, const double2 *__restrict__ f, const double *__restrict__ scal,
@@ -564,7 +700,7 @@ __global__ void k_project_f(int N, const double2 *__restrict__ f, const double *
         fp[i] = v;
         a += v.x * v.x + v.y * v.y;
     }
-    block_partials(a, 0.0, 0.0, partial);
+    block_partials(a, 0.0, 0.0, 0.0, partial);
 }
 
 __global__ void k_zero2(int N, double2 *x)
@@ -573,16 +709,16 @@ __global__ void k_zero2(int N, double2 *x)
         x[i] = make_double2(0.0, 0.0);
 }
 
-// r = f - A x with ||r||^2 partials (one row per thread group; the epilogue
-// accumulates into a per-thread register that the block reduces at the end)
-template <int T>
-__global__ void __launch_bounds__(256) k_resid_norm(int N, const int *__restrict__ rp,
+// FP64 finest-level operator with a reduction epilogue (block CSR form, T lanes).
+// MODE 0: out = A x, partial x.(A x).  MODE 1: out = f - A x (if out), partials
+// ||f - A x||^2 and sum of x_u.
+template <int T, int MODE>
+__global__ void __launch_bounds__(256) k_bsr_reduce(int N, const int *__restrict__ rp,
                                                      const int *__restrict__ ci,
-                                                     const double2 *__restrict__ v,
+                                                     const double *__restrict__ v,
                                                      const double2 *__restrict__ x,
                                                      const double2 *__restrict__ f,
-                                                     double2 *__restrict__ r, double *partial,
-                                                     int want_xmean)
+                                                     double2 *__restrict__ out, double *partial)
 {
     const int lane = threadIdx.x & (T - 1);
     const int groups = (gridDim.x * blockDim.x) / T;
@@ -596,10 +732,10 @@ __global__ void __launch_bounds__(256) k_resid_norm(int N, const int *__restrict
         const int e = act ? rp[p + 1] : 0;
         for (int t = act ? rp[p] + lane : 0; t < e; t += T) {
             const int q = ci[t];
-            const double2 a01 = v[2 * (size_t)t], a23 = v[2 * (size_t)t + 1];
+            const BlkS<double> a = load_blk(v, (size_t)t);
             const double2 xq = x[q];
-            y0 = fma(a01.x, xq.x, fma(a01.y, xq.y, y0));
-            y1 = fma(a23.x, xq.x, fma(a23.y, xq.y, y1));
+            y0 = fma(a.a00, xq.x, fma(a.a01, xq.y, y0));
+            y1 = fma(a.a10, xq.x, fma(a.a11, xq.y, y1));
         }
 #pragma unroll
         for (int o = T / 2; o > 0; o >>= 1) {
@@ -607,113 +743,23 @@ __global__ void __launch_bounds__(256) k_resid_norm(int N, const int *__restrict
             y1 += __shfl_xor_sync(0xffffffffu, y1, o, T);
         }
         if (act && lane == 0) {
-            double2 fp = f[p];
-            double r0 = fp.x - y0, r1 = fp.y - y1;
-            if (r) r[p] = make_double2(r0, r1);
-            acc += r0 * r0 + r1 * r1;
-            if (want_xmean) xs += x[p].y;
+            const double2 xp = x[p];
+            if (MODE == 0) {
+                out[p] = make_double2(y0, y1);
+                acc += xp.x * y0 + xp.y * y1;
+            } else {
+                const double2 fp = f[p];
+                const double r0 = fp.x - y0, r1 = fp.y - y1;
+                if (out) out[p] = make_double2(r0, r1);
+                acc += r0 * r0 + r1 * r1;
+                xs += xp.y;
+            }
         }
     }
-    block_partials(acc, xs, 0.0, partial);
+    block_partials(acc, xs, 0.0, 0.0, partial);
 }
 
-// q = A p with p.q partials
-template <int T>
-__global__ void __launch_bounds__(256) k_apply_dot(int N, const int *__restrict__ rp,
-                                                    const int *__restrict__ ci,
-                                                    const double2 *__restrict__ v,
-                                                    const double2 *__restrict__ p_,
-                                                    double2 *__restrict__ q, double *partial)
-{
-    const int lane = threadIdx.x & (T - 1);
-    const int groups = (gridDim.x * blockDim.x) / T;
-    const int warp_first = ((blockIdx.x * blockDim.x + threadIdx.x) & ~31) / T;
-    const int g_in_warp = (threadIdx.x & 31) / T;
-    double acc = 0.0;
-    for (int pw = warp_first; pw < N; pw += groups) {
-        const int p = pw + g_in_warp;
-        const bool act = p < N;
-        double y0 = 0.0, y1 = 0.0;
-        const int e = act ? rp[p + 1] : 0;
-        for (int t = act ? rp[p] + lane : 0; t < e; t += T) {
-            const int c = ci[t];
-            const double2 a01 = v[2 * (size_t)t], a23 = v[2 * (size_t)t + 1];
-            const double2 xq = p_[c];
-            y0 = fma(a01.x, xq.x, fma(a01.y, xq.y, y0));
-            y1 = fma(a23.x, xq.x, fma(a23.y, xq.y, y1));
-        }
-#pragma unroll
-        for (int o = T / 2; o > 0; o >>= 1) {
-            y0 += __shfl_xor_sync(0xffffffffu, y0, o, T);
-            y1 += __shfl_xor_sync(0xffffffffu, y1, o, T);
-        }
-        if (act && lane == 0) {
-            q[p] = make_double2(y0, y1);
-            double2 pp = p_[p];
-            acc += pp.x * y0 + pp.y * y1;
-        }
-    }
-    block_partials(acc, 0.0, 0.0, partial);
-}
-
-__global__ void k_z_stats(int N, const double2 *__restrict__ z, const double2 *__restrict__ r,
-                          double *partial)
-{
-    double a = 0.0, b = 0.0, c = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        double2 zi = z[i], ri = r[i];
-        a += zi.y;
-        b += ri.y;
-        c += ri.x * zi.x + ri.y * zi.y;
-    }
-    block_partials(a, b, c, partial);
-}
-
-// p = z (first iteration: p holds no previous direction) or p = z + beta p
-__global__ void k_p_update(int N, double2 *__restrict__ z, double2 *__restrict__ p,
-                           const double *__restrict__ scal, int first)
-{
-    double mz = scal[S_MEANZ], beta = scal[S_BETA];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        double2 zi = z[i];
-        zi.y -= mz;
-        z[i] = zi;
-        if (first) {
-            p[i] = zi;
-        } else {
-            double2 pi = p[i];
-            p[i] = make_double2(zi.x + beta * pi.x, zi.y + beta * pi.y);
-        }
-    }
-}
-
-__global__ void k_xr_update(int N, double2 *__restrict__ x, double2 *__restrict__ r,
-                            const double2 *__restrict__ p, const double2 *__restrict__ q,
-                            const double *__restrict__ scal, double *partial)
-{
-    double alpha = scal[S_ALPHA], acc = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        double2 xi = x[i], ri = r[i], pi = p[i], qi = q[i];
-        xi.x += alpha * pi.x;
-        xi.y += alpha * pi.y;
-        ri.x -= alpha * qi.x;
-        ri.y -= alpha * qi.y;
-        x[i] = xi;
-        r[i] = ri;
-        acc += ri.x * ri.x + ri.y * ri.y;
-    }
-    block_partials(acc, 0.0, 0.0, partial);
-}
-
-__global__ void k_project_x(int N, double2 *__restrict__ x, const double *__restrict__ scal)
-{
-    double m = scal[S_MEANX];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) x[i].y -= m;
-}
-
-// Sliced-ELL finest-level operator with a reduction epilogue.
-// MODE 0: out = A x, partial x.(A x).  MODE 1: out = f - A x (if out), partials
-// ||f - A x||^2 and sum of x_u.
+// Same with the sliced-ELL finest level.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_sell_reduce(int N, const int *__restrict__ sptr,
                                                       const int *__restrict__ col,
@@ -749,71 +795,126 @@ __global__ void __launch_bounds__(256) k_sell_reduce(int N, const int *__restric
             xs += xp.y;
         }
     }
-    block_partials(acc, xs, 0.0, partial);
+    block_partials(acc, xs, 0.0, 0.0, partial);
 }
 
-template <int T>
-static void launch_resid_norm(const BSR &A, const double2 *x, const double2 *f, double2 *r,
-                              double *partial, int want_xmean, cudaStream_t s)
+template <int MODE>
+static void fine_reduce(const amg_hierarchy *h, const double2 *x, const double2 *f, double2 *out,
+                        double *partial, cudaStream_t s)
 {
-    k_resid_norm<T><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, (const double2 *)A.v.p, x, f, r,
-                                               partial, want_xmean); ::bd::note_launch();
-}
-
-template <int T>
-static void launch_apply_dot(const BSR &A, const double2 *p, double2 *q, double *partial, cudaStream_t s)
-{
-    k_apply_dot<T><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, (const double2 *)A.v.p, p, q, partial); ::bd::note_launch();
-}
-
-static void resid_norm(const amg_hierarchy *h, const BSR &A, int T, const double2 *x,
-                       const double2 *f, double2 *r, double *partial, int want_xmean, cudaStream_t s)
-{
+    const Level &L0 = h->lev[0];
     if (h->sell.valid) {
         const FineSell &F = h->sell;
-        k_sell_reduce<1><<<kRedBlocks, 256, 0, s>>>(A.nbr, F.sptr.p, F.col.p, (const double2 *)F.kk.p,
-                                                    F.cm.p, x, f, r, partial); ::bd::note_launch();
+        k_sell_reduce<MODE><<<kRedBlocks, 256, 0, s>>>(L0.N, F.sptr.p, F.col.p, (const double2 *)F.kk.p,
+                                                       F.cm.p, x, f, out, partial); ::bd::note_launch();
         return;
     }
-    switch (T) {
-    case 1: launch_resid_norm<1>(A, x, f, r, partial, want_xmean, s); break;
-    case 2: launch_resid_norm<2>(A, x, f, r, partial, want_xmean, s); break;
-    case 4: launch_resid_norm<4>(A, x, f, r, partial, want_xmean, s); break;
-    case 8: launch_resid_norm<8>(A, x, f, r, partial, want_xmean, s); break;
-    case 16: launch_resid_norm<16>(A, x, f, r, partial, want_xmean, s); break;
-    default: launch_resid_norm<32>(A, x, f, r, partial, want_xmean, s); break;
+    const BSR &A = L0.A;
+    switch (lanes_for(A)) {
+    case 1: k_bsr_reduce<1, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, partial); ::bd::note_launch(); break;
+    case 2: k_bsr_reduce<2, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, partial); ::bd::note_launch(); break;
+    case 4: k_bsr_reduce<4, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, partial); ::bd::note_launch(); break;
+    case 8: k_bsr_reduce<8, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, partial); ::bd::note_launch(); break;
+    case 16: k_bsr_reduce<16, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, partial); ::bd::note_launch(); break;
+    default: k_bsr_reduce<32, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, partial); ::bd::note_launch(); break;
     }
 }
 
-static void apply_dot(const amg_hierarchy *h, const BSR &A, int T, const double2 *p, double2 *q,
-                      double *partial, cudaStream_t s)
+// sums of z_u and r_u, r.z and (flexible form) r.z_old
+__global__ void k_z_stats(int N, const double2 *__restrict__ z, const double2 *__restrict__ r,
+                          const double2 *__restrict__ zold, double *partial)
 {
-    if (h->sell.valid) {
-        const FineSell &F = h->sell;
-        k_sell_reduce<0><<<kRedBlocks, 256, 0, s>>>(A.nbr, F.sptr.p, F.col.p, (const double2 *)F.kk.p,
-                                                    F.cm.p, p, nullptr, q, partial); ::bd::note_launch();
-        return;
+    double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const double2 zi = z[i], ri = r[i];
+        a += zi.y;
+        b += ri.y;
+        c += ri.x * zi.x + ri.y * zi.y;
+        if (zold) {
+            const double2 oi = zold[i];
+            d += ri.x * oi.x + ri.y * oi.y;
+        }
     }
-    switch (T) {
-    case 1: launch_apply_dot<1>(A, p, q, partial, s); break;
-    case 2: launch_apply_dot<2>(A, p, q, partial, s); break;
-    case 4: launch_apply_dot<4>(A, p, q, partial, s); break;
-    case 8: launch_apply_dot<8>(A, p, q, partial, s); break;
-    case 16: launch_apply_dot<16>(A, p, q, partial, s); break;
-    default: launch_apply_dot<32>(A, p, q, partial, s); break;
+    block_partials(a, b, c, d, partial);
+}
+
+// z <- z - mean(z_u) e_u; p = z (first iteration) or z + beta p; keeps the
+// projected z for the next flexible beta when zold is given
+__global__ void k_p_update(int N, double2 *__restrict__ z, double2 *__restrict__ p,
+                           double2 *__restrict__ zold, const double *__restrict__ scal, int first)
+{
+    const double mz = scal[S_MEANZ], beta = scal[S_BETA];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        double2 zi = z[i];
+        zi.y -= mz;
+        z[i] = zi;
+        if (zold) zold[i] = zi;
+        if (first) {
+            p[i] = zi;
+        } else {
+            const double2 pi = p[i];
+            p[i] = make_double2(zi.x + beta * pi.x, zi.y + beta * pi.y);
+        }
     }
 }
 
+__global__ void k_xr_update(int N, double2 *__restrict__ x, double2 *__restrict__ r,
+                            const double2 *__restrict__ p, const double2 *__restrict__ q,
+                            const double *__restrict__ scal, double *partial)
+{
+    const double alpha = scal[S_ALPHA];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        double2 xi = x[i], ri = r[i];
+        const double2 pi = p[i], qi = q[i];
+        xi.x += alpha * pi.x;
+        xi.y += alpha * pi.y;
+        ri.x -= alpha * qi.x;
+        ri.y -= alpha * qi.y;
+        x[i] = xi;
+        r[i] = ri;
+        acc += ri.x * ri.x + ri.y * ri.y;
+    }
+    block_partials(acc, 0.0, 0.0, 0.0, partial);
+}
+
+__global__ void k_project_x(int N, double2 *__restrict__ x, const double *__restrict__ scal)
+{
+    const double m = scal[S_MEANX];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) x[i].y -= m;
+}
+
+// ------------------------------------------------------------------ workspace
 int prepare_solve(amg_hierarchy *h)
 {
+    const bool p32 = h->prec32;
     for (int l = 0; l < h->nlev; l++) {
         Level &L = h->lev[l];
         size_t n = 2 * (size_t)L.N;
-        BD_TRY(L.f.alloc(n));
-        BD_TRY(L.u.alloc(n));
-        BD_TRY(L.r.alloc(n));
-        BD_TRY(L.d.alloc(n));
-        BD_TRY(L.w.alloc(n));
+        if (p32) {
+            BD_TRY(L.f32.alloc(n));
+            BD_TRY(L.u32.alloc(n));
+            BD_TRY(L.r32.alloc(n));
+            BD_TRY(L.d32.alloc(n));
+            BD_TRY(L.w32.alloc(n));
+            BD_TRY(L.invdiag32.alloc(n));
+            BD_TRY(L.A32.alloc(4 * (size_t)L.A.nb));
+            k_to_f32<<<grid_for(n, 256), 256>>>((long long)n, L.invdiag.p, L.invdiag32.p); ::bd::note_launch();
+            k_to_f32<<<grid_for(4 * L.A.nb, 256), 256>>>(4 * L.A.nb, L.A.v.p, L.A32.p); ::bd::note_launch();
+            if (l < h->nlev - 1) {
+                BD_TRY(L.P32.alloc(4 * (size_t)L.P.nb));
+                BD_TRY(L.R32.alloc(4 * (size_t)L.R.nb));
+                k_to_f32<<<grid_for(4 * L.P.nb, 256), 256>>>(4 * L.P.nb, L.P.v.p, L.P32.p); ::bd::note_launch();
+                k_to_f32<<<grid_for(4 * L.R.nb, 256), 256>>>(4 * L.R.nb, L.R.v.p, L.R32.p); ::bd::note_launch();
+            }
+            BD_LAUNCH_CHECK();
+        } else {
+            BD_TRY(L.f.alloc(n));
+            BD_TRY(L.u.alloc(n));
+            BD_TRY(L.r.alloc(n));
+            BD_TRY(L.d.alloc(n));
+            BD_TRY(L.w.alloc(n));
+        }
         if (l < h->nlev - 1) {
             double lo = h->opts.eig_lo * L.lam, hi = h->opts.eig_hi * L.lam;
             double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
@@ -824,6 +925,15 @@ int prepare_solve(amg_hierarchy *h)
             L.ch_c2 = 2.0 * rho1 / delta;
         }
     }
+    if (p32 && h->sell.valid) {
+        FineSell &F = h->sell;
+        size_t nk = 64 * (size_t)F.slots;
+        BD_TRY(F.kk32.alloc(nk));
+        BD_TRY(F.cm32.alloc((size_t)h->lev[0].N));
+        k_to_f32<<<grid_for(nk, 256), 256>>>((long long)nk, F.kk.p, F.kk32.p); ::bd::note_launch();
+        k_to_f32<<<grid_for(h->lev[0].N, 256), 256>>>(h->lev[0].N, F.cm.p, F.cm32.p); ::bd::note_launch();
+        BD_LAUNCH_CHECK();
+    }
     size_t n0 = 2 * (size_t)h->lev[0].N;
     BD_TRY(h->x.alloc(n0));
     BD_TRY(h->r.alloc(n0));
@@ -831,9 +941,11 @@ int prepare_solve(amg_hierarchy *h)
     BD_TRY(h->p.alloc(n0));
     BD_TRY(h->q.alloc(n0));
     BD_TRY(h->fp.alloc(n0));
-    BD_TRY(h->partial.alloc(3 * (size_t)kRedBlocks));
+    if (p32) BD_TRY(h->zold.alloc(n0));
+    BD_TRY(h->partial.alloc(kPart * (size_t)kRedBlocks));
     BD_TRY(h->scal.alloc(S_NSLOTS));
     if (!h->host_scal) BD_CUDA(cudaMallocHost((void **)&h->host_scal, sizeof(double) * S_NSLOTS));
+    BD_CUDA(cudaDeviceSynchronize());
     return BD_OK;
 }
 
@@ -844,15 +956,18 @@ static int read_scal(amg_hierarchy *h, cudaStream_t s)
     return BD_OK;
 }
 
-// Projected PCG on device vectors (f_dev, x_dev: 2N doubles each).
+// Projected PCG on device vectors (f_dev, x_dev: 2N doubles each).  With an
+// FP32 V-cycle the preconditioner is not exactly symmetric, so beta takes the
+// flexible (Polak-Ribiere) form.
 int pcg_solve_device(amg_hierarchy *h, const double *f_dev, double *x_dev, int warm,
                      const solve_options *o, cudaStream_t s, solve_info *info)
 {
     Level &L0 = h->lev[0];
     const int N = L0.N;
-    const int T = lanes_for(L0.A);
+    const int flex = h->prec32 ? 1 : 0;
     double2 *x = (double2 *)x_dev, *r = (double2 *)h->r.p, *z = (double2 *)h->z.p;
     double2 *p = (double2 *)h->p.p, *q = (double2 *)h->q.p, *fp = (double2 *)h->fp.p;
+    double2 *zold = flex ? (double2 *)h->zold.p : nullptr;
     double *part = h->partial.p, *scal = h->scal.p;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     BD_CUDA(cudaEventCreate(&e0));
@@ -861,12 +976,14 @@ int pcg_solve_device(amg_hierarchy *h, const double *f_dev, double *x_dev, int w
     BD_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * S_NSLOTS, s));
     const int G = kRedBlocks;
     k_f_stats<<<G, 256, 0, s>>>(N, (const double2 *)f_dev, part); ::bd::note_launch();
-    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 0, N, 0); ::bd::note_launch();
+    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 0, N, 0, flex); ::bd::note_launch();
     k_project_f<<<G, 256, 0, s>>>(N, (const double2 *)f_dev, scal, fp, part); ::bd::note_launch();
-    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 1, N, 0); ::bd::note_launch();
-    if (!warm) k_zero2<<<G, 256, 0, s>>>(N, x); ::bd::note_launch();
-    resid_norm(h, L0.A, T, x, fp, r, part, 0, s);
-    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 2, N, 0); ::bd::note_launch();
+    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 1, N, 0, flex); ::bd::note_launch();
+    if (!warm) {
+        k_zero2<<<G, 256, 0, s>>>(N, x); ::bd::note_launch();
+    }
+    fine_reduce<1>(h, x, fp, r, part, s);
+    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 2, N, 0, flex); ::bd::note_launch();
     BD_LAUNCH_CHECK();
     BD_TRY(read_scal(h, s));
     double ff = h->host_scal[S_FF], sumfu = h->host_scal[S_SUMFU];
@@ -885,15 +1002,15 @@ int pcg_solve_device(amg_hierarchy *h, const double *f_dev, double *x_dev, int w
         status = BD_ENOTCONV;
         while (it < o->max_it) {
             BD_TRY(vcycle_device(h, (const double *)r, (double *)z, s));
-            k_z_stats<<<G, 256, 0, s>>>(N, z, r, part); ::bd::note_launch();
-            k_finish<<<1, 1024, 0, s>>>(part, G, scal, 3, N, it == 0); ::bd::note_launch();
-            k_p_update<<<G, 256, 0, s>>>(N, z, p, scal, it == 0); ::bd::note_launch();
-            int sq = prof_begin(h, s);
-            apply_dot(h, L0.A, T, p, q, part, s);
-            prof_end(h, sq, fine_bytes(h, L0, 2), fine_flops(h, L0), s);
-            k_finish<<<1, 1024, 0, s>>>(part, G, scal, 4, N, 0); ::bd::note_launch();
+            k_z_stats<<<G, 256, 0, s>>>(N, z, r, it == 0 ? nullptr : zold, part); ::bd::note_launch();
+            k_finish<<<1, 1024, 0, s>>>(part, G, scal, 3, N, it == 0, flex); ::bd::note_launch();
+            k_p_update<<<G, 256, 0, s>>>(N, z, p, zold, scal, it == 0); ::bd::note_launch();
+            int sq = h->prec32 ? -1 : prof_begin(h, s);
+            fine_reduce<0>(h, p, nullptr, q, part, s);
+            prof_end(h, sq, fine_bytes<double>(h, L0, 2), fine_flops(L0), s);
+            k_finish<<<1, 1024, 0, s>>>(part, G, scal, 4, N, 0, flex); ::bd::note_launch();
             k_xr_update<<<G, 256, 0, s>>>(N, x, r, p, q, scal, part); ::bd::note_launch();
-            k_finish<<<1, 1024, 0, s>>>(part, G, scal, 2, N, 0); ::bd::note_launch();
+            k_finish<<<1, 1024, 0, s>>>(part, G, scal, 2, N, 0, flex); ::bd::note_launch();
             BD_LAUNCH_CHECK();
             BD_TRY(read_scal(h, s));
             it++;
@@ -913,8 +1030,8 @@ int pcg_solve_device(amg_hierarchy *h, const double *f_dev, double *x_dev, int w
         }
     }
     // true residual and projection of x
-    resid_norm(h, L0.A, T, x, fp, nullptr, part, 1, s);
-    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 5, N, 0); ::bd::note_launch();
+    fine_reduce<1>(h, x, fp, nullptr, part, s);
+    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 5, N, 0, flex); ::bd::note_launch();
     k_project_x<<<G, 256, 0, s>>>(N, x, scal); ::bd::note_launch();
     BD_LAUNCH_CHECK();
     BD_CUDA(cudaEventRecord(e1, s));
@@ -970,6 +1087,7 @@ extern "C" int amg_profile_read(const amg_hierarchy *h, amg_kernel_profile *out)
 {
     if (!h || !out) return BD_EINVAL;
     *out = h->prof_sum;
+    out->precision = h->prec32 ? 1 : 0;
     return BD_OK;
 }
 

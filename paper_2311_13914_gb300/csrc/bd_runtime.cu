@@ -542,6 +542,7 @@ extern "C" void amg_options_default(amg_options *o)
     o->eig_lo = 0.05;
     o->eig_hi = 1.05;
     o->seed = 0;
+    o->precision = 0;
 }
 
 extern "C" void solve_options_default(solve_options *o)

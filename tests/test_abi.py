@@ -61,6 +61,7 @@ def test_defaults_match_oracle(L, oracle_lib):
     for k in ("theta", "coarse_eq_limit", "max_levels", "cheb_degree", "esteig_steps", "eig_lo",
               "eig_hi", "seed", "square_levels"):
         assert getattr(o, k) == d[k], k
+    assert o.precision == 0  # the plain FP64 form is the default
     rm = L.bd_rm_params_default()
     for k, v in oracle_lib.RM_PARAMS.items():
         assert getattr(rm, k) == v
@@ -78,6 +79,6 @@ def test_struct_layouts_match_header(L):
     # field order and sizes of the public structs (all naturally aligned)
     assert C.sizeof(L.Mesh) == 3 * 4 + 4 + 3 * 8
     assert C.sizeof(L.Params) == 7 * 8
-    assert C.sizeof(L.AmgOptions) == 8 + 5 * 4 + 4 + 2 * 8 + 8
+    assert C.sizeof(L.AmgOptions) == 8 + 5 * 4 + 4 + 2 * 8 + 8 + 4 + 4
     assert C.sizeof(L.SolveOptions) == 8 + 3 * 4 + 4
     assert C.sizeof(L.SolveInfo) == 2 * 4 + 3 * 8 + 8

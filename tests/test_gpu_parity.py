@@ -247,6 +247,51 @@ def test_time_stepping_matches_oracle(B, oracle_lib):
     assert ginfo["total_iters"] > 0
 
 
+@pytest.mark.parametrize("mi", [0, 1, 3])
+def test_fp32_vcycle_flexible_pcg_matches_fp64_oracle(B, oracle_lib, mi):
+    """FP32 V-cycle inside the FP64 flexible CG: the outer loop still drives the
+    FP64 residual to rtol 1e-8, so the solution meets the same 1e-7 bound
+    against the FP64 oracle; the iteration count may grow slightly."""
+    m = MESHES[mi]
+    fib = W.fibre_table(m)
+    sysh = B.bd_assemble(m, W.DEFAULT_PARAMS, fib)
+    h32 = B.amg_setup(sysh, B.amg_options_default(precision=1))
+    h64 = B.amg_setup(sysh)
+    o = oracle_lib.assemble(m, W.DEFAULT_PARAMS, fib)
+    H = oracle_lib.Hierarchy(o["A"])
+    f = W.rhs(o["A"].shape[0], seed=10 + mi)
+    x32, i32 = B.amg_solve(h32, f)
+    x64, i64 = B.amg_solve(h64, f)
+    xo, io = H.pcg(f, rtol=1e-8)
+    assert i32["status"] == 0 and i32["true_rel_res"] <= 1.01e-8
+    assert np.linalg.norm(x32 - xo) <= 1e-7 * np.linalg.norm(xo)
+    assert i32["iters"] <= i64["iters"] + 3
+    # one FP32 V-cycle agrees with the FP64 one to FP32 accuracy
+    r = W.rhs(o["A"].shape[0], seed=20 + mi)
+    z32, z64 = B.amg_vcycle(h32, r), B.amg_vcycle(h64, r)
+    assert np.linalg.norm(z32 - z64) <= 1e-4 * np.linalg.norm(z64)
+
+
+def test_fp32_time_stepping_matches_oracle(B, oracle_lib):
+    m = W.mesh(16, 16, 8, 0.6, 0.6, 0.3)
+    p = W.DEFAULT_PARAMS
+    fib = W.fibre_table(m, 120.0, 10.0)
+    stim = W.stimulus(m)
+    sysh = B.bd_assemble(m, p, fib)
+    h = B.amg_setup(sysh, B.amg_options_default(precision=1))
+    sim = B.bd_sim_create(sysh, h, stim=stim, stim_ms=1.0)
+    o = oracle_lib.assemble(m, p, fib)
+    H = oracle_lib.Hierarchy(o["A"])
+    N = W.n_nodes(m)
+    v, ue, w = np.zeros(N), np.zeros(N), np.zeros(N)
+    for k in range(25):
+        H.bd_step(o["M"], p, stim if k * p["dt"] < 1.0 else np.zeros(N), v, ue, w)
+    B.bd_step(sim, 25)
+    gv, gu, gw = B.bd_sim_get_state(sim, N)
+    for a, b in ((gv, v), (gu, ue), (gw, w)):
+        assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b)
+
+
 def test_full_size_slab_properties(B):
     """128x128x32 slab (1.1M unknowns): bit-symmetric operator, zero row sums
     of the stiffness part, total mass, converged solve with projected u_e."""
