@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 
 T_STEPS = 100           # time steps per simulation
 STIM_MS = 1.0           # stimulus duration
+PROFILED_SOLVES = 2     # solves per step timed launch by launch (the rest run as graphs)
 FP64_ALU_PEAK = 152 * 2 * 2 * 2.07e9   # SMs x DFMA/clk/SM x flop/FMA x max SM clock
 FP32_ALU_PEAK = 152 * 128 * 2 * 2.07e9  # SMs x FP32 lanes/SM x flop/FMA x max SM clock
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -237,10 +238,18 @@ def run_ours(args):
         sysh = B.bd_assemble(mesh, p, fib_d, stream=stream)
         h = B.amg_setup(sysh, amg_opts(B, args), stream=stream)
         ev[1].record(stream)
-        if profile:
-            B.amg_profile_enable(h, True)
         sim = B.bd_sim_create(sysh, h, stim=stim_d, stim_ms=STIM_MS, stream=stream)
-        info = B.bd_step(sim, T, stream=stream)
+        total_iters = 0
+        if profile and T > PROFILED_SOLVES:
+            # live timing of the dominant kernel on the first solves (host-driven
+            # loop, CUDA events per launch); the rest run as whole-solve graphs
+            B.amg_profile_enable(h, True)
+            total_iters += B.bd_step(sim, PROFILED_SOLVES, stream=stream)["total_iters"]
+            B.amg_profile_enable(h, False)
+            info = B.bd_step(sim, T - PROFILED_SOLVES, stream=stream)
+        else:
+            info = B.bd_step(sim, T, stream=stream)
+        info["total_iters"] += total_iters
         ev[2].record(stream)
         stream.synchronize()
         if record is not None:
@@ -249,7 +258,7 @@ def run_ours(args):
             record["iters"].append(info["total_iters"] / max(T, 1))
             record["true_rel_res"].append(info["true_rel_res"])
             if profile:
-                pr = B.amg_profile_read(h)
+                pr = B.amg_profile_read(h)  # sums survive disabling
                 for k in ("launches", "total_ms", "bytes", "flops"):
                     record["prof_" + k] += pr[k]
                 record["prof_precision"] = pr["precision"]

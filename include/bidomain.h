@@ -201,6 +201,12 @@ int amg_export_level(const amg_hierarchy *h, int level, int *a_row_ptr, int *a_c
 int amg_vcycle(amg_hierarchy *h, const double *r, double *z, int on_device, void *stream);
 
 /* ---- a11: projected PCG solve of A x = f ----------------------------------
+ * Runs as one CUDA graph per solve (built on the first solve and reused): the
+ * iteration loop is a WHILE node whose condition the last reduction kernel of
+ * each iteration sets on the device (converged, breakdown, or max_it reached),
+ * so the host synchronises once per solve.  A hierarchy serves one solve at a
+ * time.  With profiling on or strict mode, a host-driven loop with the same
+ * kernels in the same order runs instead (identical results).
  * f, x: n = 2N doubles, host or device.  f is projected orthogonal to (0,1)
  * (Euclidean mean of the u_e entries removed) unless opts->strict, in which
  * case a relative null-space part above 1e-8 returns BD_EINCONSISTENT.  On
@@ -215,7 +221,10 @@ void amg_destroy(amg_hierarchy *h);
  * SpMV launches of the V-cycle, and of PCG when the V-cycle is FP64) is
  * bracketed by CUDA events on the launching stream; the durations, the algorithmic bytes (matrix values and
  * indices once, each vector stream once) and the flops (2 per scalar nonzero)
- * are summed.  Enabling resets the sums; reading requires no pending work. */
+ * are summed.  Switching it on resets the sums, switching it off keeps them
+ * for amg_profile_read; reading requires no pending work.  While it is on,
+ * solves run the host-driven loop (one launch at a time) instead of the
+ * whole-solve CUDA graph. */
 typedef struct {
     long long launches;
     double total_ms;

@@ -56,7 +56,15 @@ struct amg_hierarchy {
     bd::DBuf<double> cinv, zc;
     double zz = 0.0;
     // PCG workspace on the finest level
-    bd::DBuf<double> x, r, z, p, q, fp, zold;
+    bd::DBuf<double> x, r, z, p, q, fp, zold, fin;
+    // whole-solve CUDA graph: pre-loop, a device-controlled WHILE node over one
+    // PCG iteration, post-loop (built on first use, reused by every solve)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
+    bool graph_failed = false;
+    long long graph_pre = 0, graph_body = 0, graph_post = 0;  // kernel nodes per section
+    double *host_init = nullptr;  // pinned initial scalar block for a graph launch
     bd::DBuf<double> partial;   // kRedBlocks x 4 partial sums
     bd::DBuf<double> scal;      // device scalars of the PCG recurrences
     double *host_scal = nullptr;  // pinned mirror
@@ -69,6 +77,11 @@ struct amg_hierarchy {
     amg_kernel_profile prof_sum{};
     ~amg_hierarchy() {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (cap_stream2) cudaStreamDestroy(cap_stream2);
+        if (host_init) cudaFreeHost(host_init);
     }
 };
 

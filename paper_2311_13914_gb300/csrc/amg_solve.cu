@@ -12,6 +12,7 @@
 // deterministic: fixed grid, per-block partial sums, one finishing block.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <new>
 
 #include "amg_internal.cuh"
@@ -565,7 +566,10 @@ int vcycle_device(amg_hierarchy *h, const double *r_dev, double *z_dev, cudaStre
 // scal[] slots of the device scalars
 enum {
     S_SUMFU = 0, S_FF, S_NF2, S_RR, S_RZ, S_PQ, S_ALPHA, S_BETA, S_MEANZ,
-    S_BREAK, S_MEANF, S_TRR, S_MEANX, S_NSLOTS
+    S_BREAK, S_MEANF, S_TRR, S_MEANX,
+    // device-side loop control of the graph form
+    S_RTOL, S_MAXIT, S_WARM, S_IT, S_STATUS,
+    S_NSLOTS
 };
 constexpr int kPart = 4;  // partial sums per block
 
@@ -609,8 +613,11 @@ __device__ __forceinline__ void block_partials(double a, double b, double c, dou
 }
 
 // Reduce the per-block partial sums in a fixed order, then apply `stage`.
+// first < 0: read "first iteration" from the device iteration counter (graph form).
+// Stages 6 and 7 are the graph form's loop control: 6 opens the loop after the
+// initial residual, 7 closes an iteration; both set the WHILE node's condition.
 __global__ void k_finish(const double *__restrict__ partial, int nparts, double *scal, int stage,
-                         int N, int first, int flexible)
+                         int N, int first, int flexible, cudaGraphConditionalHandle cond)
 {
     __shared__ double red[kPart][32];
     double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
@@ -643,6 +650,7 @@ __global__ void k_finish(const double *__restrict__ partial, int nparts, double 
         c += red[2][i];
         d += red[3][i];
     }
+    if (first < 0) first = scal[S_IT] == 0.0;
     switch (stage) {
     case 0:  // f statistics: sum f_u, ||f||^2
         scal[S_SUMFU] = a;
@@ -676,7 +684,43 @@ __global__ void k_finish(const double *__restrict__ partial, int nparts, double 
         scal[S_TRR] = a;
         scal[S_MEANX] = b / N;
         break;
+    case 6: {  // initial ||r||^2; open the loop unless already converged
+        scal[S_RR] = a;
+        const double nf = sqrt(scal[S_NF2]);
+        const bool go = nf > 0.0 && !(sqrt(a) <= scal[S_RTOL] * nf) && scal[S_MAXIT] > 0.0;
+        scal[S_IT] = 0.0;
+        scal[S_STATUS] = go ? (double)BD_ENOTCONV : (double)BD_OK;
+        cudaGraphSetConditional(cond, go ? 1u : 0u);
+        break;
     }
+    case 7: {  // ||r||^2 after the update; close or continue the loop
+        scal[S_RR] = a;
+        const double it = scal[S_IT] + 1.0;
+        scal[S_IT] = it;
+        const double nf = sqrt(scal[S_NF2]), rr = sqrt(a);
+        bool go = true;
+        if (scal[S_BREAK] != 0.0 || !isfinite(rr)) {
+            scal[S_STATUS] = (double)BD_EBREAKDOWN;
+            go = false;
+        } else if (rr <= scal[S_RTOL] * nf) {
+            scal[S_STATUS] = (double)BD_OK;
+            go = false;
+        } else if (it >= scal[S_MAXIT]) {
+            go = false;  // status stays BD_ENOTCONV
+        }
+        cudaGraphSetConditional(cond, go ? 1u : 0u);
+        break;
+    }
+    }
+}
+
+// x = 0 when (mode 0) the solve is cold, or (mode 1) the right-hand side is zero
+__global__ void k_zero_if(int N, double2 *__restrict__ x, const double *__restrict__ scal, int mode)
+{
+    const bool z = mode == 0 ? scal[S_WARM] == 0.0 : scal[S_NF2] == 0.0;
+    if (!z) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        x[i] = make_double2(0.0, 0.0);
 }
 
 __global__ void k_f_stats(int N, const double2 *__restrict__ f, double *partial)
@@ -844,6 +888,7 @@ __global__ void k_p_update(int N, double2 *__restrict__ z, double2 *__restrict__
                            double2 *__restrict__ zold, const double *__restrict__ scal, int first)
 {
     const double mz = scal[S_MEANZ], beta = scal[S_BETA];
+    if (first < 0) first = scal[S_IT] == 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         double2 zi = z[i];
         zi.y -= mz;
@@ -941,10 +986,15 @@ int prepare_solve(amg_hierarchy *h)
     BD_TRY(h->p.alloc(n0));
     BD_TRY(h->q.alloc(n0));
     BD_TRY(h->fp.alloc(n0));
-    if (p32) BD_TRY(h->zold.alloc(n0));
+    BD_TRY(h->fin.alloc(n0));
+    if (p32) {
+        BD_TRY(h->zold.alloc(n0));
+        BD_CUDA(cudaMemset(h->zold.p, 0, h->zold.bytes()));
+    }
     BD_TRY(h->partial.alloc(kPart * (size_t)kRedBlocks));
     BD_TRY(h->scal.alloc(S_NSLOTS));
     if (!h->host_scal) BD_CUDA(cudaMallocHost((void **)&h->host_scal, sizeof(double) * S_NSLOTS));
+    if (!h->host_init) BD_CUDA(cudaMallocHost((void **)&h->host_init, sizeof(double) * S_NSLOTS));
     BD_CUDA(cudaDeviceSynchronize());
     return BD_OK;
 }
@@ -956,11 +1006,12 @@ static int read_scal(amg_hierarchy *h, cudaStream_t s)
     return BD_OK;
 }
 
-// Projected PCG on device vectors (f_dev, x_dev: 2N doubles each).  With an
-// FP32 V-cycle the preconditioner is not exactly symmetric, so beta takes the
-// flexible (Polak-Ribiere) form.
-int pcg_solve_device(amg_hierarchy *h, const double *f_dev, double *x_dev, int warm,
-                     const solve_options *o, cudaStream_t s, solve_info *info)
+// Projected PCG on device vectors (f_dev, x_dev: 2N doubles each), host-driven
+// loop: one residual read-back per iteration.  With an FP32 V-cycle the
+// preconditioner is not exactly symmetric, so beta takes the flexible
+// (Polak-Ribiere) form.
+static int pcg_solve_loop(amg_hierarchy *h, const double *f_dev, double *x_dev, int warm,
+                          const solve_options *o, cudaStream_t s, solve_info *info)
 {
     Level &L0 = h->lev[0];
     const int N = L0.N;
@@ -976,14 +1027,14 @@ int pcg_solve_device(amg_hierarchy *h, const double *f_dev, double *x_dev, int w
     BD_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * S_NSLOTS, s));
     const int G = kRedBlocks;
     k_f_stats<<<G, 256, 0, s>>>(N, (const double2 *)f_dev, part); ::bd::note_launch();
-    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 0, N, 0, flex); ::bd::note_launch();
+    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 0, N, 0, flex, 0); ::bd::note_launch();
     k_project_f<<<G, 256, 0, s>>>(N, (const double2 *)f_dev, scal, fp, part); ::bd::note_launch();
-    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 1, N, 0, flex); ::bd::note_launch();
+    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 1, N, 0, flex, 0); ::bd::note_launch();
     if (!warm) {
         k_zero2<<<G, 256, 0, s>>>(N, x); ::bd::note_launch();
     }
     fine_reduce<1>(h, x, fp, r, part, s);
-    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 2, N, 0, flex); ::bd::note_launch();
+    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 2, N, 0, flex, 0); ::bd::note_launch();
     BD_LAUNCH_CHECK();
     BD_TRY(read_scal(h, s));
     double ff = h->host_scal[S_FF], sumfu = h->host_scal[S_SUMFU];
@@ -1003,14 +1054,14 @@ int pcg_solve_device(amg_hierarchy *h, const double *f_dev, double *x_dev, int w
         while (it < o->max_it) {
             BD_TRY(vcycle_device(h, (const double *)r, (double *)z, s));
             k_z_stats<<<G, 256, 0, s>>>(N, z, r, it == 0 ? nullptr : zold, part); ::bd::note_launch();
-            k_finish<<<1, 1024, 0, s>>>(part, G, scal, 3, N, it == 0, flex); ::bd::note_launch();
+            k_finish<<<1, 1024, 0, s>>>(part, G, scal, 3, N, it == 0, flex, 0); ::bd::note_launch();
             k_p_update<<<G, 256, 0, s>>>(N, z, p, zold, scal, it == 0); ::bd::note_launch();
             int sq = h->prec32 ? -1 : prof_begin(h, s);
             fine_reduce<0>(h, p, nullptr, q, part, s);
             prof_end(h, sq, fine_bytes<double>(h, L0, 2), fine_flops(L0), s);
-            k_finish<<<1, 1024, 0, s>>>(part, G, scal, 4, N, 0, flex); ::bd::note_launch();
+            k_finish<<<1, 1024, 0, s>>>(part, G, scal, 4, N, 0, flex, 0); ::bd::note_launch();
             k_xr_update<<<G, 256, 0, s>>>(N, x, r, p, q, scal, part); ::bd::note_launch();
-            k_finish<<<1, 1024, 0, s>>>(part, G, scal, 2, N, 0, flex); ::bd::note_launch();
+            k_finish<<<1, 1024, 0, s>>>(part, G, scal, 2, N, 0, flex, 0); ::bd::note_launch();
             BD_LAUNCH_CHECK();
             BD_TRY(read_scal(h, s));
             it++;
@@ -1031,7 +1082,7 @@ int pcg_solve_device(amg_hierarchy *h, const double *f_dev, double *x_dev, int w
     }
     // true residual and projection of x
     fine_reduce<1>(h, x, fp, nullptr, part, s);
-    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 5, N, 0, flex); ::bd::note_launch();
+    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 5, N, 0, flex, 0); ::bd::note_launch();
     k_project_x<<<G, 256, 0, s>>>(N, x, scal); ::bd::note_launch();
     BD_LAUNCH_CHECK();
     BD_CUDA(cudaEventRecord(e1, s));
@@ -1049,6 +1100,164 @@ int pcg_solve_device(amg_hierarchy *h, const double *f_dev, double *x_dev, int w
         info->solve_ms = ms;
     }
     return status;
+}
+
+// ------------------------------------------------------------------ graph form
+// The whole solve as one CUDA graph: the pre-loop kernels, a WHILE node whose
+// body is one PCG iteration (V-cycle included), the post-loop kernels.  The
+// body's last reduction decides convergence, breakdown or max_it on the device
+// and sets the node's condition, so a solve costs one graph launch and one
+// host synchronisation.  The loop is bounded by max_it.  The graph works on the
+// hierarchy's own buffers (right-hand side in `fin`, iterate in `x`).
+static void end_capture_quietly(cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(s, &g);
+        if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+}
+
+static int capture_graph(amg_hierarchy *h)
+{
+    Level &L0 = h->lev[0];
+    const int N = L0.N, G = kRedBlocks;
+    const int flex = h->prec32 ? 1 : 0;
+    cudaStream_t s = h->cap_stream, s2 = h->cap_stream2;
+    double2 *x = (double2 *)h->x.p, *r = (double2 *)h->r.p, *z = (double2 *)h->z.p;
+    double2 *p = (double2 *)h->p.p, *q = (double2 *)h->q.p, *fp = (double2 *)h->fp.p;
+    double2 *zold = flex ? (double2 *)h->zold.p : nullptr;
+    const double2 *fin = (const double2 *)h->fin.p;
+    double *part = h->partial.p, *scal = h->scal.p;
+    // kernel-node counts per section (the launch counter counts executions, so
+    // the increments made while capturing are taken back below)
+    const long long c0 = launch_count();
+    BD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    k_f_stats<<<G, 256, 0, s>>>(N, fin, part); ::bd::note_launch();
+    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 0, N, 0, flex, 0); ::bd::note_launch();
+    k_project_f<<<G, 256, 0, s>>>(N, fin, scal, fp, part); ::bd::note_launch();
+    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 1, N, 0, flex, 0); ::bd::note_launch();
+    k_zero_if<<<G, 256, 0, s>>>(N, x, scal, 0); ::bd::note_launch();
+    fine_reduce<1>(h, x, fp, r, part, s);
+    BD_LAUNCH_CHECK();
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    BD_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphConditionalHandle cond;
+    BD_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 0, 0));
+    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 6, N, 0, flex, cond); ::bd::note_launch();
+    BD_LAUNCH_CHECK();
+    BD_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    BD_CUDA(cudaGraphAddNode(&wnode, g, deps, nullptr, nd, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    const long long c1 = launch_count();
+    BD_CUDA(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    BD_TRY(vcycle_device(h, (const double *)r, (double *)z, s2));
+    k_z_stats<<<G, 256, 0, s2>>>(N, z, r, zold, part); ::bd::note_launch();
+    k_finish<<<1, 1024, 0, s2>>>(part, G, scal, 3, N, -1, flex, 0); ::bd::note_launch();
+    k_p_update<<<G, 256, 0, s2>>>(N, z, p, zold, scal, -1); ::bd::note_launch();
+    fine_reduce<0>(h, p, nullptr, q, part, s2);
+    k_finish<<<1, 1024, 0, s2>>>(part, G, scal, 4, N, 0, flex, 0); ::bd::note_launch();
+    k_xr_update<<<G, 256, 0, s2>>>(N, x, r, p, q, scal, part); ::bd::note_launch();
+    k_finish<<<1, 1024, 0, s2>>>(part, G, scal, 7, N, 0, flex, cond); ::bd::note_launch();
+    BD_LAUNCH_CHECK();
+    cudaGraph_t body_out = nullptr;
+    BD_CUDA(cudaStreamEndCapture(s2, &body_out));
+    const long long c2 = launch_count();
+    BD_CUDA(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    k_zero_if<<<G, 256, 0, s>>>(N, x, scal, 1); ::bd::note_launch();
+    fine_reduce<1>(h, x, fp, nullptr, part, s);
+    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 5, N, 0, flex, 0); ::bd::note_launch();
+    k_project_x<<<G, 256, 0, s>>>(N, x, scal); ::bd::note_launch();
+    BD_LAUNCH_CHECK();
+    const long long c3 = launch_count();
+    h->graph_pre = c1 - c0;
+    h->graph_body = c2 - c1;
+    h->graph_post = c3 - c2;
+    note_launches(-(c3 - c0));
+    BD_CUDA(cudaStreamEndCapture(s, &h->graph));
+    BD_CUDA(cudaGraphInstantiate(&h->graph_exec, h->graph, 0));
+    return BD_OK;
+}
+
+static int build_graph(amg_hierarchy *h)
+{
+    if (!h->cap_stream) BD_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    if (!h->cap_stream2) BD_CUDA(cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking));
+    int st = capture_graph(h);
+    if (st != BD_OK) {
+        end_capture_quietly(h->cap_stream2);
+        end_capture_quietly(h->cap_stream);
+        if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+        if (h->graph) cudaGraphDestroy(h->graph);
+        h->graph_exec = nullptr;
+        h->graph = nullptr;
+    }
+    return st;
+}
+
+static int pcg_solve_graph(amg_hierarchy *h, const double *f_dev, double *x_dev, int warm,
+                           const solve_options *o, cudaStream_t s, solve_info *info)
+{
+    const size_t bytes = sizeof(double) * 2 * (size_t)h->lev[0].N;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BD_CUDA(cudaEventCreate(&e0));
+    BD_CUDA(cudaEventCreate(&e1));
+    BD_CUDA(cudaEventRecord(e0, s));
+    if (f_dev != h->fin.p) BD_CUDA(cudaMemcpyAsync(h->fin.p, f_dev, bytes, cudaMemcpyDeviceToDevice, s));
+    if (warm && x_dev != h->x.p) BD_CUDA(cudaMemcpyAsync(h->x.p, x_dev, bytes, cudaMemcpyDeviceToDevice, s));
+    for (int i = 0; i < S_NSLOTS; i++) h->host_init[i] = 0.0;
+    h->host_init[S_RTOL] = o->rtol;
+    h->host_init[S_MAXIT] = (double)o->max_it;
+    h->host_init[S_WARM] = warm ? 1.0 : 0.0;
+    BD_CUDA(cudaMemcpyAsync(h->scal.p, h->host_init, sizeof(double) * S_NSLOTS, cudaMemcpyHostToDevice, s));
+    BD_CUDA(cudaGraphLaunch(h->graph_exec, s));
+    if (x_dev != h->x.p) BD_CUDA(cudaMemcpyAsync(x_dev, h->x.p, bytes, cudaMemcpyDeviceToDevice, s));
+    BD_CUDA(cudaEventRecord(e1, s));
+    BD_TRY(read_scal(h, s));
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const double *sc = h->host_scal;
+    const double nf = sqrt(sc[S_NF2]);
+    const int status = (int)sc[S_STATUS];
+    note_launches(h->graph_pre + h->graph_post + (long long)sc[S_IT] * h->graph_body);
+    if (info) {
+        info->status = status;
+        info->iters = (int)sc[S_IT];
+        info->rel_res = nf > 0.0 ? sqrt(sc[S_RR]) / nf : 0.0;
+        info->true_rel_res = nf > 0.0 ? sqrt(sc[S_TRR]) / nf : 0.0;
+        info->solve_ms = ms;
+    }
+    return status;
+}
+
+// The graph form unless live kernel timing is on (its CUDA events bracket
+// single launches), strict mode is requested (checked on the host before the
+// loop), the graph could not be built, or BD_SOLVE_GRAPH=0 is set.
+int pcg_solve_device(amg_hierarchy *h, const double *f_dev, double *x_dev, int warm,
+                     const solve_options *o, cudaStream_t s, solve_info *info)
+{
+    static const bool graph_off = [] {
+        const char *e = getenv("BD_SOLVE_GRAPH");
+        return e && e[0] == '0';
+    }();
+    if (!h->prof && !o->strict && !h->graph_failed && !graph_off) {
+        if (!h->graph_exec && build_graph(h) != BD_OK) h->graph_failed = true;
+        if (h->graph_exec) return pcg_solve_graph(h, f_dev, x_dev, warm, o, s, info);
+    }
+    return pcg_solve_loop(h, f_dev, x_dev, warm, o, s, info);
 }
 
 }  // namespace bd
@@ -1078,8 +1287,8 @@ extern "C" int amg_profile_enable(amg_hierarchy *h, int enable)
 {
     if (!h) return BD_EINVAL;
     prof_collect(h);
+    if (enable && !h->prof) h->prof_sum = amg_kernel_profile{};  // fresh sums when switched on
     h->prof = enable ? 1 : 0;
-    h->prof_sum = amg_kernel_profile{};
     return BD_OK;
 }
 

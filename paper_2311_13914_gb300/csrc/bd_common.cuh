@@ -17,6 +17,8 @@ namespace bd {
 // Every kernel launch of the library calls note_launch(); bd_launch_count()
 // reports the running total (host-side, atomic).
 void note_launch();
+void note_launches(long long n);  // adds n (may be negative: undo capture-time counts)
+long long launch_count();
 
 // ------------------------------------------------------------------ errors
 void record_cuda_error(cudaError_t e, const char *what, const char *file, int line);

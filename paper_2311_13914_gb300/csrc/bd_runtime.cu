@@ -14,6 +14,8 @@ static thread_local char g_last_err[256];
 static std::atomic<long long> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 void record_cuda_error(cudaError_t e, const char *what, const char *file, int line)
 {

@@ -223,6 +223,27 @@ def test_solve_edge_cases(B, oracle_lib):
     assert np.array_equal(xd.cpu().numpy(), xh)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_solve_equals_host_loop_solve(B, precision):
+    """The whole-solve CUDA graph (device-side WHILE loop) and the host-driven
+    loop run the same kernels in the same order with deterministic reductions:
+    identical iterates, iteration counts and statuses."""
+    m = MESHES[3]
+    sysh = B.bd_assemble(m, W.DEFAULT_PARAMS, W.fibre_table(m))
+    h = B.amg_setup(sysh, B.amg_options_default(precision=precision))
+    n = 2 * W.n_nodes(m)
+    for seed, opts in ((1, {}), (2, dict(max_it=3, rtol=1e-14)), (3, dict(rtol=1e-3))):
+        f = W.rhs(n, seed)
+        o = B.solve_options_default(**opts)
+        xg, ig = B.amg_solve(h, f, opts=o, raise_on_error=False)       # graph form
+        B.amg_profile_enable(h, True)                                   # timed launches: host loop
+        xl, il = B.amg_solve(h, f, opts=o, raise_on_error=False)
+        B.amg_profile_enable(h, False)
+        assert ig["iters"] == il["iters"] and ig["status"] == il["status"]
+        assert np.array_equal(xg, xl)
+        assert ig["true_rel_res"] == il["true_rel_res"]
+
+
 def test_time_stepping_matches_oracle(B, oracle_lib):
     m = W.mesh(16, 16, 8, 0.6, 0.6, 0.3)
     p = W.DEFAULT_PARAMS
