@@ -7,7 +7,7 @@ namespace bd {
 
 constexpr int kMaxLevels = 16;
 constexpr int kMaxCoarse = 4096;   // unknowns of the dense coarsest level
-constexpr int kRedBlocks = 608;    // partial-sum blocks of the solve reductions (4 x SMs)
+constexpr int kRedBlocks = 1216;   // blocks of the solve's reduction kernels (8 x SMs)
 
 struct Level {
     int N = 0;                 // nodes (unknowns 2N)
@@ -66,6 +66,7 @@ struct amg_hierarchy {
     long long graph_pre = 0, graph_body = 0, graph_post = 0;  // kernel nodes per section
     double *host_init = nullptr;  // pinned initial scalar block for a graph launch
     bd::DBuf<double> partial;   // kRedBlocks x 4 partial sums
+    bd::DBuf<unsigned int> counter;  // arrival counter of the last-block reductions
     bd::DBuf<double> scal;      // device scalars of the PCG recurrences
     double *host_scal = nullptr;  // pinned mirror
     bd::DBuf<long long> exact_acc;

@@ -78,6 +78,49 @@ __global__ void __launch_bounds__(256) k_bsr(int N, const int *__restrict__ rp,
     }
 }
 
+// Long rows on small levels (few hundred to a few thousand block rows of
+// hundreds of blocks): a whole thread block of TB threads per row, so that each
+// thread walks only a few blocks; warp shuffles then shared memory reduce.
+template <int TB, class S, class G, class E>
+__global__ void __launch_bounds__(TB) k_bsr_wide(int N, const int *__restrict__ rp,
+                                                  const int *__restrict__ ci,
+                                                  const S *__restrict__ v, G gather, E epi)
+{
+    __shared__ S red[2][TB / 32];
+    for (int p = blockIdx.x; p < N; p += gridDim.x) {
+        S y0 = 0, y1 = 0;
+        const int e = rp[p + 1];
+        for (int t = rp[p] + threadIdx.x; t < e; t += TB) {
+            const int q = ci[t];
+            const BlkS<S> a = load_blk(v, (size_t)t);
+            const v2<S> x = gather(q);
+            y0 = fma(a.a00, x.x, fma(a.a01, x.y, y0));
+            y1 = fma(a.a10, x.x, fma(a.a11, x.y, y1));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+            y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+        }
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) {
+            red[0][w] = y0;
+            red[1][w] = y1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            S a0 = 0, a1 = 0;
+#pragma unroll
+            for (int i = 0; i < TB / 32; i++) {
+                a0 += red[0][i];
+                a1 += red[1][i];
+            }
+            epi(p, a0, a1);
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------ finest level, sliced ELL
 // One thread per row; slot j of slice s holds entry j of its 32 rows
 // contiguously, so every slot is one coalesced (Ki, Ke) load and one 128-byte
@@ -93,6 +136,7 @@ __global__ void __launch_bounds__(256) k_sell(int N, const int *__restrict__ spt
         const int sl = p >> 5, lane = p & 31;
         const int j1 = sptr[sl + 1];
         S a = 0, b = 0;
+#pragma unroll 4
         for (int j = sptr[sl]; j < j1; j++) {
             const size_t idx = (size_t)j * 32 + lane;
             const int q = col[idx];
@@ -243,8 +287,18 @@ static int launch_bsr(const BSR &A, const S *vals, int T, G g, E e, cudaStream_t
     int N = A.nbr;
     if (N <= 0) return BD_OK;
     const int threads = 256;
-    long long groups_per_block = threads / T;
+    long long groups_per_block = T >= 64 ? 1 : threads / T;
     int grid = (int)std::min<long long>((N + groups_per_block - 1) / groups_per_block, (long long)kSM * 16);
+    if (T >= 64) {
+        int gw = (int)std::min<long long>(N, (long long)kSM * 32);
+        switch (T) {
+        case 64: k_bsr_wide<64, S><<<gw, 64, 0, s>>>(N, A.rp.p, A.ci.p, vals, g, e); ::bd::note_launch(); break;
+        case 128: k_bsr_wide<128, S><<<gw, 128, 0, s>>>(N, A.rp.p, A.ci.p, vals, g, e); ::bd::note_launch(); break;
+        default: k_bsr_wide<256, S><<<gw, 256, 0, s>>>(N, A.rp.p, A.ci.p, vals, g, e); ::bd::note_launch(); break;
+        }
+        BD_LAUNCH_CHECK();
+        return BD_OK;
+    }
     switch (T) {
     case 1: k_bsr<1, S><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, vals, g, e); ::bd::note_launch(); break;
     case 2: k_bsr<2, S><<<grid, threads, 0, s>>>(N, A.rp.p, A.ci.p, vals, g, e); ::bd::note_launch(); break;
@@ -257,15 +311,23 @@ static int launch_bsr(const BSR &A, const S *vals, int T, G g, E e, cudaStream_t
     return BD_OK;
 }
 
-// Lanes per block row.  Every lane-level reduction step costs adds that are
-// scarce in FP64 on this part, so rows are handled by as few lanes as their
-// length allows (one thread per row for short rows); small levels get more
-// lanes per row so that the grid still fills the GPU.
-static int lanes_for(const BSR &A)
+// Lanes per block row.  Every lane-level reduction step costs adds, which are
+// scarce in FP64 on this part, so FP64 rows use as few lanes as their length
+// allows (one thread per row for short rows).  FP32 adds are cheap, so FP32
+// rows use more lanes to shorten each thread's chain of dependent loads.
+// Levels with few, long rows (the dense-ish coarse levels) take a whole thread
+// block per row; small levels get more lanes so the grid still fills the GPU.
+static int lanes_for(const BSR &A, bool fp32)
 {
     double avg = A.nbr > 0 ? (double)A.nb / A.nbr : 1.0;
-    int T = avg <= 40 ? 1 : (avg <= 160 ? 4 : (avg <= 640 ? 8 : 16));
+    int T;
+    if (fp32) T = avg <= 12 ? 1 : (avg <= 48 ? 4 : (avg <= 160 ? 16 : 32));
+    else T = avg <= 40 ? 1 : (avg <= 160 ? 4 : (avg <= 640 ? 8 : 16));
     while (T < 32 && (long long)A.nbr * T < 65536) T <<= 1;
+    if ((long long)A.nbr * 32 < 131072 && avg > 96) {  // few long rows: a block per row
+        T = 64;
+        while (T < 256 && T * 3 < avg) T <<= 1;
+    }
     return T;
 }
 
@@ -339,7 +401,7 @@ static int apply_level(amg_hierarchy *h, int l, const LV<S> &lv, G g, E e, cudaS
         BD_LAUNCH_CHECK();
         return BD_OK;
     }
-    return launch_bsr<S>(L.A, lv.Av, lanes_for(L.A), g, e, s);
+    return launch_bsr<S>(L.A, lv.Av, lanes_for(L.A, sizeof(S) == 4), g, e, s);
 }
 
 // ------------------------------------------------------------------ live kernel timing
@@ -504,7 +566,7 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
         prof_end(h, sr, fine_bytes<S>(h, L, 3), fine_flops(L), s);
         const Level &C = h->lev[l + 1];
         const LV<S> cv = view<S>(h, l + 1);
-        BD_TRY(launch_bsr<S>(L.R, lv.Rv, lanes_for(L.R), GatherVec<S>{lv.r},
+        BD_TRY(launch_bsr<S>(L.R, lv.Rv, lanes_for(L.R, sizeof(S) == 4), GatherVec<S>{lv.r},
                              EpiStoreD0<S>{cv.f, cv.d, cv.invd, (S)C.ch_inv_theta}, s));
     }
     {
@@ -521,7 +583,7 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
         const v2<S> *f = l == 0 ? f0 : lv.f;
         v2<S> *u = l == 0 ? u0 : lv.u;
         const LV<S> cv = view<S>(h, l + 1);
-        BD_TRY(launch_bsr<S>(L.P, lv.Pv, lanes_for(L.P), GatherVec<S>{cv.u}, EpiAdd<S>{u}, s));
+        BD_TRY(launch_bsr<S>(L.P, lv.Pv, lanes_for(L.P, sizeof(S) == 4), GatherVec<S>{cv.u}, EpiAdd<S>{u}, s));
         int s1 = l == 0 ? prof_begin(h, s) : -1;
         BD_TRY(apply_level<S>(h, l, lv, GatherVec<S>{u},
                               EpiPost1<S>{f, lv.invd, u, lv.r, lv.d, lv.w, (S)L.ch_inv_theta}, s));
@@ -573,85 +635,25 @@ enum {
 };
 constexpr int kPart = 4;  // partial sums per block
 
-__device__ __forceinline__ void block_partials(double a, double b, double c, double d, double *partial)
-{
-    __shared__ double red[kPart][32];
-    for (int o = 16; o; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-        c += __shfl_xor_sync(0xffffffffu, c, o);
-        d += __shfl_xor_sync(0xffffffffu, d, o);
-    }
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) {
-        red[0][w] = a;
-        red[1][w] = b;
-        red[2][w] = c;
-        red[3][w] = d;
-    }
-    __syncthreads();
-    if (w == 0) {
-        int nw = blockDim.x >> 5;
-        a = l < nw ? red[0][l] : 0.0;
-        b = l < nw ? red[1][l] : 0.0;
-        c = l < nw ? red[2][l] : 0.0;
-        d = l < nw ? red[3][l] : 0.0;
-        for (int o = 16; o; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            b += __shfl_xor_sync(0xffffffffu, b, o);
-            c += __shfl_xor_sync(0xffffffffu, c, o);
-            d += __shfl_xor_sync(0xffffffffu, d, o);
-        }
-        if (l == 0) {
-            double *o_ = partial + kPart * blockIdx.x;
-            o_[0] = a;
-            o_[1] = b;
-            o_[2] = c;
-            o_[3] = d;
-        }
-    }
-}
+// What the last block of a reduction kernel does with the totals.
+// first < 0: "first iteration" is read from the device iteration counter
+// (graph form).  Stages 6 and 7 are the graph form's loop control: 6 opens
+// the loop after the initial residual, 7 closes an iteration; both set the
+// WHILE node's condition.
+struct Fin {
+    double *scal;
+    double *partial;
+    unsigned int *counter;
+    int stage, N, first, flex;
+    cudaGraphConditionalHandle cond;
+};
 
-// Reduce the per-block partial sums in a fixed order, then apply `stage`.
-// first < 0: read "first iteration" from the device iteration counter (graph form).
-// Stages 6 and 7 are the graph form's loop control: 6 opens the loop after the
-// initial residual, 7 closes an iteration; both set the WHILE node's condition.
-__global__ void k_finish(const double *__restrict__ partial, int nparts, double *scal, int stage,
-                         int N, int first, int flexible, cudaGraphConditionalHandle cond)
+__device__ void finish_stage(const Fin &f, double a, double b, double c, double d)
 {
-    __shared__ double red[kPart][32];
-    double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-        const double *q = partial + kPart * i;
-        a += q[0];
-        b += q[1];
-        c += q[2];
-        d += q[3];
-    }
-    for (int o = 16; o; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-        c += __shfl_xor_sync(0xffffffffu, c, o);
-        d += __shfl_xor_sync(0xffffffffu, d, o);
-    }
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) {
-        red[0][w] = a;
-        red[1][w] = b;
-        red[2][w] = c;
-        red[3][w] = d;
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    a = b = c = d = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
-        a += red[0][i];
-        b += red[1][i];
-        c += red[2][i];
-        d += red[3][i];
-    }
-    if (first < 0) first = scal[S_IT] == 0.0;
-    switch (stage) {
+    double *scal = f.scal;
+    const int N = f.N;
+    const int first = f.first < 0 ? (scal[S_IT] == 0.0) : f.first;
+    switch (f.stage) {
     case 0:  // f statistics: sum f_u, ||f||^2
         scal[S_SUMFU] = a;
         scal[S_FF] = b;
@@ -669,17 +671,16 @@ __global__ void k_finish(const double *__restrict__ partial, int nparts, double 
         scal[S_MEANZ] = mz;
         // standard CG: beta = rz_new / rz_old; flexible (Polak-Ribiere):
         // beta = (r.z_new - r.z_old) / rz_old with z_old the previous projected z
-        double num = flexible ? rz - d : rz;
+        double num = f.flex ? rz - d : rz;
         scal[S_BETA] = first ? 0.0 : num / scal[S_RZ];
         scal[S_RZ] = rz;
         break;
     }
-    case 4: {  // p.q
+    case 4:  // p.q
         scal[S_PQ] = a;
         if (!(a > 0.0) || !isfinite(a) || !isfinite(scal[S_RZ])) scal[S_BREAK] = 1.0;
         scal[S_ALPHA] = scal[S_RZ] / a;
         break;
-    }
     case 5:  // true residual and mean of x_u
         scal[S_TRR] = a;
         scal[S_MEANX] = b / N;
@@ -690,7 +691,7 @@ __global__ void k_finish(const double *__restrict__ partial, int nparts, double 
         const bool go = nf > 0.0 && !(sqrt(a) <= scal[S_RTOL] * nf) && scal[S_MAXIT] > 0.0;
         scal[S_IT] = 0.0;
         scal[S_STATUS] = go ? (double)BD_ENOTCONV : (double)BD_OK;
-        cudaGraphSetConditional(cond, go ? 1u : 0u);
+        cudaGraphSetConditional(f.cond, go ? 1u : 0u);
         break;
     }
     case 7: {  // ||r||^2 after the update; close or continue the loop
@@ -708,10 +709,108 @@ __global__ void k_finish(const double *__restrict__ partial, int nparts, double 
         } else if (it >= scal[S_MAXIT]) {
             go = false;  // status stays BD_ENOTCONV
         }
-        cudaGraphSetConditional(cond, go ? 1u : 0u);
+        cudaGraphSetConditional(f.cond, go ? 1u : 0u);
         break;
     }
     }
+}
+
+// Block sums -> partial[blockIdx]; the last block to arrive reduces all
+// partials in a fixed order (independent of which block is last, so the
+// result is reproducible) and applies the stage.  No waiting: blocks that are
+// not last simply exit.
+__device__ __forceinline__ void reduce4(double &a, double &b, double &c, double &d, double (*red)[32])
+{
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        d += __shfl_xor_sync(0xffffffffu, d, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0) {
+        red[0][w] = a;
+        red[1][w] = b;
+        red[2][w] = c;
+        red[3][w] = d;
+    }
+    __syncthreads();
+    if (w == 0) {
+        a = l < nw ? red[0][l] : 0.0;
+        b = l < nw ? red[1][l] : 0.0;
+        c = l < nw ? red[2][l] : 0.0;
+        d = l < nw ? red[3][l] : 0.0;
+        for (int o = 16; o; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            d += __shfl_xor_sync(0xffffffffu, d, o);
+        }
+    }
+}
+
+__device__ void block_finish(double a, double b, double c, double d, const Fin &f)
+{
+    __shared__ double red[kPart][32];
+    __shared__ bool last;
+    reduce4(a, b, c, d, red);
+    if (threadIdx.x == 0) {
+        double *o = f.partial + kPart * blockIdx.x;
+        o[0] = a;
+        o[1] = b;
+        o[2] = c;
+        o[3] = d;
+        __threadfence();
+        const unsigned int ticket = atomicAdd(f.counter, 1u);
+        last = ticket == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    a = b = c = d = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        const volatile double *q = f.partial + kPart * i;
+        a += q[0];
+        b += q[1];
+        c += q[2];
+        d += q[3];
+    }
+    __syncthreads();
+    reduce4(a, b, c, d, red);
+    if (threadIdx.x == 0) {
+        finish_stage(f, a, b, c, d);
+        *f.counter = 0u;
+    }
+}
+
+__global__ void k_f_stats(int N, const double2 *__restrict__ f, Fin fin)
+{
+    double a = 0.0, b = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        double2 v = f[i];
+        a += v.y;
+        b += v.x * v.x + v.y * v.y;
+    }
+    block_finish(a, b, 0.0, 0.0, fin);
+}
+
+__global__ void k_project_f(int N, const double2 *__restrict__ f, double2 *__restrict__ fp, Fin fin)
+{
+    const double m = fin.scal[S_MEANF];
+    double a = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        double2 v = f[i];
+        v.y -= m;
+        fp[i] = v;
+        a += v.x * v.x + v.y * v.y;
+    }
+    block_finish(a, 0.0, 0.0, 0.0, fin);
+}
+
+__global__ void k_zero2(int N, double2 *x)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        x[i] = make_double2(0.0, 0.0);
 }
 
 // x = 0 when (mode 0) the solve is cold, or (mode 1) the right-hand side is zero
@@ -723,46 +822,16 @@ __global__ void k_zero_if(int N, double2 *__restrict__ x, const double *__restri
         x[i] = make_double2(0.0, 0.0);
 }
 
-__global__ void k_f_stats(int N, const double2 *__restrict__ f, double *partial)
-{
-    double a = 0.0, b = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        double2 v = f[i];
-        a += v.y;
-        b += v.x * v.x + v.y * v.y;
-    }
-    block_partials(a, b, 0.0, 0.0, partial);
-}
-
-__global__ void k_project_f(int N, const double2 *__restrict__ f, const double *__restrict__ scal,
-                            double2 *__restrict__ fp, double *partial)
-{
-    double m = scal[S_MEANF], a = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        double2 v = f[i];
-        v.y -= m;
-        fp[i] = v;
-        a += v.x * v.x + v.y * v.y;
-    }
-    block_partials(a, 0.0, 0.0, 0.0, partial);
-}
-
-__global__ void k_zero2(int N, double2 *x)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
-        x[i] = make_double2(0.0, 0.0);
-}
-
 // FP64 finest-level operator with a reduction epilogue (block CSR form, T lanes).
 // MODE 0: out = A x, partial x.(A x).  MODE 1: out = f - A x (if out), partials
-// ||f - A x||^2 and sum of x_u.
+// ||f - A x||^2 and sum of x_u.  x is in (v, u) form.
 template <int T, int MODE>
 __global__ void __launch_bounds__(256) k_bsr_reduce(int N, const int *__restrict__ rp,
                                                      const int *__restrict__ ci,
                                                      const double *__restrict__ v,
                                                      const double2 *__restrict__ x,
                                                      const double2 *__restrict__ f,
-                                                     double2 *__restrict__ out, double *partial)
+                                                     double2 *__restrict__ out, Fin fin)
 {
     const int lane = threadIdx.x & (T - 1);
     const int groups = (gridDim.x * blockDim.x) / T;
@@ -800,73 +869,78 @@ __global__ void __launch_bounds__(256) k_bsr_reduce(int N, const int *__restrict
             }
         }
     }
-    block_partials(acc, xs, 0.0, 0.0, partial);
+    block_finish(acc, xs, 0.0, 0.0, fin);
 }
 
-// Same with the sliced-ELL finest level.
-template <int MODE>
+// Same with the sliced-ELL finest level.  SU: x is stored as (v + u, u), so a
+// node pair costs two FP64 FMAs (a += Ki s, b += Ke u) instead of three.
+template <int MODE, bool SU>
 __global__ void __launch_bounds__(256) k_sell_reduce(int N, const int *__restrict__ sptr,
                                                       const int *__restrict__ col,
                                                       const double2 *__restrict__ kk,
                                                       const double *__restrict__ cm,
                                                       const double2 *__restrict__ x,
                                                       const double2 *__restrict__ f,
-                                                      double2 *__restrict__ out, double *partial)
+                                                      double2 *__restrict__ out, Fin fin)
 {
     double acc = 0.0, xs = 0.0;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
         const int sl = p >> 5, lane = p & 31;
         const int j1 = sptr[sl + 1];
         double a = 0.0, b = 0.0;
+#pragma unroll 4
         for (int j = sptr[sl]; j < j1; j++) {
             const size_t idx = (size_t)j * 32 + lane;
             const int q = col[idx];
             const double2 k = kk[idx];
             const double2 xq = x[q];
-            a = fma(k.x, xq.x + xq.y, a);
+            a = fma(k.x, SU ? xq.x : xq.x + xq.y, a);
             b = fma(k.y, xq.y, b);
         }
-        const double2 xp = x[p];
-        const double y0 = fma(cm[p], xp.x, a), y1 = a + b;
+        const double2 xs2 = x[p];
+        const double vp = SU ? xs2.x - xs2.y : xs2.x, up = xs2.y;
+        const double y0 = fma(cm[p], vp, a), y1 = a + b;
         if (MODE == 0) {
             out[p] = make_double2(y0, y1);
-            acc += xp.x * y0 + xp.y * y1;
+            acc += vp * y0 + up * y1;
         } else {
             const double2 fp = f[p];
             const double r0 = fp.x - y0, r1 = fp.y - y1;
             if (out) out[p] = make_double2(r0, r1);
             acc += r0 * r0 + r1 * r1;
-            xs += xp.y;
+            xs += up;
         }
     }
-    block_partials(acc, xs, 0.0, 0.0, partial);
+    block_finish(acc, xs, 0.0, 0.0, fin);
 }
 
+// MODE 0 applies A to the search direction (in (v+u, u) form when the finest
+// level is sliced ELL); MODE 1 forms f - A x for an iterate in (v, u) form.
 template <int MODE>
 static void fine_reduce(const amg_hierarchy *h, const double2 *x, const double2 *f, double2 *out,
-                        double *partial, cudaStream_t s)
+                        const Fin &fin, cudaStream_t s)
 {
     const Level &L0 = h->lev[0];
     if (h->sell.valid) {
         const FineSell &F = h->sell;
-        k_sell_reduce<MODE><<<kRedBlocks, 256, 0, s>>>(L0.N, F.sptr.p, F.col.p, (const double2 *)F.kk.p,
-                                                       F.cm.p, x, f, out, partial); ::bd::note_launch();
+        k_sell_reduce<MODE, MODE == 0><<<kRedBlocks, 256, 0, s>>>(L0.N, F.sptr.p, F.col.p, (const double2 *)F.kk.p,
+                                                                  F.cm.p, x, f, out, fin); ::bd::note_launch();
         return;
     }
     const BSR &A = L0.A;
-    switch (lanes_for(A)) {
-    case 1: k_bsr_reduce<1, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, partial); ::bd::note_launch(); break;
-    case 2: k_bsr_reduce<2, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, partial); ::bd::note_launch(); break;
-    case 4: k_bsr_reduce<4, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, partial); ::bd::note_launch(); break;
-    case 8: k_bsr_reduce<8, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, partial); ::bd::note_launch(); break;
-    case 16: k_bsr_reduce<16, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, partial); ::bd::note_launch(); break;
-    default: k_bsr_reduce<32, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, partial); ::bd::note_launch(); break;
+    switch (std::min(lanes_for(A, false), 32)) {
+    case 1: k_bsr_reduce<1, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, fin); ::bd::note_launch(); break;
+    case 2: k_bsr_reduce<2, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, fin); ::bd::note_launch(); break;
+    case 4: k_bsr_reduce<4, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, fin); ::bd::note_launch(); break;
+    case 8: k_bsr_reduce<8, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, fin); ::bd::note_launch(); break;
+    case 16: k_bsr_reduce<16, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, fin); ::bd::note_launch(); break;
+    default: k_bsr_reduce<32, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, fin); ::bd::note_launch(); break;
     }
 }
 
 // sums of z_u and r_u, r.z and (flexible form) r.z_old
 __global__ void k_z_stats(int N, const double2 *__restrict__ z, const double2 *__restrict__ r,
-                          const double2 *__restrict__ zold, double *partial)
+                          const double2 *__restrict__ zold, Fin fin)
 {
     double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
@@ -879,11 +953,13 @@ __global__ void k_z_stats(int N, const double2 *__restrict__ z, const double2 *_
             d += ri.x * oi.x + ri.y * oi.y;
         }
     }
-    block_partials(a, b, c, d, partial);
+    block_finish(a, b, c, d, fin);
 }
 
-// z <- z - mean(z_u) e_u; p = z (first iteration) or z + beta p; keeps the
-// projected z for the next flexible beta when zold is given
+// z <- z - mean(z_u) e_u; p = z (first iteration) or z + beta p, stored in
+// (v+u, u) form when SU; keeps the projected z for the next flexible beta
+// when zold is given.
+template <bool SU>
 __global__ void k_p_update(int N, double2 *__restrict__ z, double2 *__restrict__ p,
                            double2 *__restrict__ zold, const double *__restrict__ scal, int first)
 {
@@ -894,25 +970,27 @@ __global__ void k_p_update(int N, double2 *__restrict__ z, double2 *__restrict__
         zi.y -= mz;
         z[i] = zi;
         if (zold) zold[i] = zi;
+        const double2 zs = SU ? make_double2(zi.x + zi.y, zi.y) : zi;
         if (first) {
-            p[i] = zi;
+            p[i] = zs;
         } else {
             const double2 pi = p[i];
-            p[i] = make_double2(zi.x + beta * pi.x, zi.y + beta * pi.y);
+            p[i] = make_double2(zs.x + beta * pi.x, zs.y + beta * pi.y);
         }
     }
 }
 
+template <bool SU>
 __global__ void k_xr_update(int N, double2 *__restrict__ x, double2 *__restrict__ r,
-                            const double2 *__restrict__ p, const double2 *__restrict__ q,
-                            const double *__restrict__ scal, double *partial)
+                            const double2 *__restrict__ p, const double2 *__restrict__ q, Fin fin)
 {
-    const double alpha = scal[S_ALPHA];
+    const double alpha = fin.scal[S_ALPHA];
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         double2 xi = x[i], ri = r[i];
         const double2 pi = p[i], qi = q[i];
-        xi.x += alpha * pi.x;
+        const double pv = SU ? pi.x - pi.y : pi.x;
+        xi.x += alpha * pv;
         xi.y += alpha * pi.y;
         ri.x -= alpha * qi.x;
         ri.y -= alpha * qi.y;
@@ -920,13 +998,29 @@ __global__ void k_xr_update(int N, double2 *__restrict__ x, double2 *__restrict_
         r[i] = ri;
         acc += ri.x * ri.x + ri.y * ri.y;
     }
-    block_partials(acc, 0.0, 0.0, 0.0, partial);
+    block_finish(acc, 0.0, 0.0, 0.0, fin);
 }
 
 __global__ void k_project_x(int N, double2 *__restrict__ x, const double *__restrict__ scal)
 {
     const double m = scal[S_MEANX];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) x[i].y -= m;
+}
+
+static void p_update(const amg_hierarchy *h, int N, double2 *z, double2 *p, double2 *zold, double *scal,
+                     int first, cudaStream_t s)
+{
+    if (h->sell.valid) k_p_update<true><<<kRedBlocks, 256, 0, s>>>(N, z, p, zold, scal, first);
+    else k_p_update<false><<<kRedBlocks, 256, 0, s>>>(N, z, p, zold, scal, first);
+    note_launch();
+}
+
+static void xr_update(const amg_hierarchy *h, int N, double2 *x, double2 *r, const double2 *p,
+                      const double2 *q, const Fin &fin, cudaStream_t s)
+{
+    if (h->sell.valid) k_xr_update<true><<<kRedBlocks, 256, 0, s>>>(N, x, r, p, q, fin);
+    else k_xr_update<false><<<kRedBlocks, 256, 0, s>>>(N, x, r, p, q, fin);
+    note_launch();
 }
 
 // ------------------------------------------------------------------ workspace
@@ -992,6 +1086,8 @@ int prepare_solve(amg_hierarchy *h)
         BD_CUDA(cudaMemset(h->zold.p, 0, h->zold.bytes()));
     }
     BD_TRY(h->partial.alloc(kPart * (size_t)kRedBlocks));
+    BD_TRY(h->counter.alloc(1));
+    BD_CUDA(cudaMemset(h->counter.p, 0, sizeof(unsigned int)));
     BD_TRY(h->scal.alloc(S_NSLOTS));
     if (!h->host_scal) BD_CUDA(cudaMallocHost((void **)&h->host_scal, sizeof(double) * S_NSLOTS));
     if (!h->host_init) BD_CUDA(cudaMallocHost((void **)&h->host_init, sizeof(double) * S_NSLOTS));
@@ -1006,6 +1102,20 @@ static int read_scal(amg_hierarchy *h, cudaStream_t s)
     return BD_OK;
 }
 
+static Fin make_fin(amg_hierarchy *h, int stage, int first, cudaGraphConditionalHandle cond = 0)
+{
+    Fin f;
+    f.scal = h->scal.p;
+    f.partial = h->partial.p;
+    f.counter = h->counter.p;
+    f.stage = stage;
+    f.N = h->lev[0].N;
+    f.first = first;
+    f.flex = h->prec32 ? 1 : 0;
+    f.cond = cond;
+    return f;
+}
+
 // Projected PCG on device vectors (f_dev, x_dev: 2N doubles each), host-driven
 // loop: one residual read-back per iteration.  With an FP32 V-cycle the
 // preconditioner is not exactly symmetric, so beta takes the flexible
@@ -1015,26 +1125,23 @@ static int pcg_solve_loop(amg_hierarchy *h, const double *f_dev, double *x_dev, 
 {
     Level &L0 = h->lev[0];
     const int N = L0.N;
-    const int flex = h->prec32 ? 1 : 0;
+    const bool flex = h->prec32;
     double2 *x = (double2 *)x_dev, *r = (double2 *)h->r.p, *z = (double2 *)h->z.p;
     double2 *p = (double2 *)h->p.p, *q = (double2 *)h->q.p, *fp = (double2 *)h->fp.p;
     double2 *zold = flex ? (double2 *)h->zold.p : nullptr;
-    double *part = h->partial.p, *scal = h->scal.p;
+    double *scal = h->scal.p;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     BD_CUDA(cudaEventCreate(&e0));
     BD_CUDA(cudaEventCreate(&e1));
     BD_CUDA(cudaEventRecord(e0, s));
     BD_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * S_NSLOTS, s));
     const int G = kRedBlocks;
-    k_f_stats<<<G, 256, 0, s>>>(N, (const double2 *)f_dev, part); ::bd::note_launch();
-    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 0, N, 0, flex, 0); ::bd::note_launch();
-    k_project_f<<<G, 256, 0, s>>>(N, (const double2 *)f_dev, scal, fp, part); ::bd::note_launch();
-    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 1, N, 0, flex, 0); ::bd::note_launch();
+    k_f_stats<<<G, 256, 0, s>>>(N, (const double2 *)f_dev, make_fin(h, 0, 0)); ::bd::note_launch();
+    k_project_f<<<G, 256, 0, s>>>(N, (const double2 *)f_dev, fp, make_fin(h, 1, 0)); ::bd::note_launch();
     if (!warm) {
         k_zero2<<<G, 256, 0, s>>>(N, x); ::bd::note_launch();
     }
-    fine_reduce<1>(h, x, fp, r, part, s);
-    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 2, N, 0, flex, 0); ::bd::note_launch();
+    fine_reduce<1>(h, x, fp, r, make_fin(h, 2, 0), s);
     BD_LAUNCH_CHECK();
     BD_TRY(read_scal(h, s));
     double ff = h->host_scal[S_FF], sumfu = h->host_scal[S_SUMFU];
@@ -1053,15 +1160,12 @@ static int pcg_solve_loop(amg_hierarchy *h, const double *f_dev, double *x_dev, 
         status = BD_ENOTCONV;
         while (it < o->max_it) {
             BD_TRY(vcycle_device(h, (const double *)r, (double *)z, s));
-            k_z_stats<<<G, 256, 0, s>>>(N, z, r, it == 0 ? nullptr : zold, part); ::bd::note_launch();
-            k_finish<<<1, 1024, 0, s>>>(part, G, scal, 3, N, it == 0, flex, 0); ::bd::note_launch();
-            k_p_update<<<G, 256, 0, s>>>(N, z, p, zold, scal, it == 0); ::bd::note_launch();
+            k_z_stats<<<G, 256, 0, s>>>(N, z, r, it == 0 ? nullptr : zold, make_fin(h, 3, it == 0)); ::bd::note_launch();
+            p_update(h, N, z, p, zold, scal, it == 0, s);
             int sq = h->prec32 ? -1 : prof_begin(h, s);
-            fine_reduce<0>(h, p, nullptr, q, part, s);
+            fine_reduce<0>(h, p, nullptr, q, make_fin(h, 4, 0), s);
             prof_end(h, sq, fine_bytes<double>(h, L0, 2), fine_flops(L0), s);
-            k_finish<<<1, 1024, 0, s>>>(part, G, scal, 4, N, 0, flex, 0); ::bd::note_launch();
-            k_xr_update<<<G, 256, 0, s>>>(N, x, r, p, q, scal, part); ::bd::note_launch();
-            k_finish<<<1, 1024, 0, s>>>(part, G, scal, 2, N, 0, flex, 0); ::bd::note_launch();
+            xr_update(h, N, x, r, p, q, make_fin(h, 2, 0), s);
             BD_LAUNCH_CHECK();
             BD_TRY(read_scal(h, s));
             it++;
@@ -1081,8 +1185,7 @@ static int pcg_solve_loop(amg_hierarchy *h, const double *f_dev, double *x_dev, 
         }
     }
     // true residual and projection of x
-    fine_reduce<1>(h, x, fp, nullptr, part, s);
-    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 5, N, 0, flex, 0); ::bd::note_launch();
+    fine_reduce<1>(h, x, fp, nullptr, make_fin(h, 5, 0), s);
     k_project_x<<<G, 256, 0, s>>>(N, x, scal); ::bd::note_launch();
     BD_LAUNCH_CHECK();
     BD_CUDA(cudaEventRecord(e1, s));
@@ -1124,23 +1227,20 @@ static int capture_graph(amg_hierarchy *h)
 {
     Level &L0 = h->lev[0];
     const int N = L0.N, G = kRedBlocks;
-    const int flex = h->prec32 ? 1 : 0;
+    const bool flex = h->prec32;
     cudaStream_t s = h->cap_stream, s2 = h->cap_stream2;
     double2 *x = (double2 *)h->x.p, *r = (double2 *)h->r.p, *z = (double2 *)h->z.p;
     double2 *p = (double2 *)h->p.p, *q = (double2 *)h->q.p, *fp = (double2 *)h->fp.p;
     double2 *zold = flex ? (double2 *)h->zold.p : nullptr;
     const double2 *fin = (const double2 *)h->fin.p;
-    double *part = h->partial.p, *scal = h->scal.p;
+    double *scal = h->scal.p;
     // kernel-node counts per section (the launch counter counts executions, so
     // the increments made while capturing are taken back below)
     const long long c0 = launch_count();
     BD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    k_f_stats<<<G, 256, 0, s>>>(N, fin, part); ::bd::note_launch();
-    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 0, N, 0, flex, 0); ::bd::note_launch();
-    k_project_f<<<G, 256, 0, s>>>(N, fin, scal, fp, part); ::bd::note_launch();
-    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 1, N, 0, flex, 0); ::bd::note_launch();
+    k_f_stats<<<G, 256, 0, s>>>(N, fin, make_fin(h, 0, 0)); ::bd::note_launch();
+    k_project_f<<<G, 256, 0, s>>>(N, fin, fp, make_fin(h, 1, 0)); ::bd::note_launch();
     k_zero_if<<<G, 256, 0, s>>>(N, x, scal, 0); ::bd::note_launch();
-    fine_reduce<1>(h, x, fp, r, part, s);
     BD_LAUNCH_CHECK();
     cudaStreamCaptureStatus cs;
     cudaGraph_t g = nullptr;
@@ -1149,7 +1249,7 @@ static int capture_graph(amg_hierarchy *h)
     BD_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
     cudaGraphConditionalHandle cond;
     BD_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 0, 0));
-    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 6, N, 0, flex, cond); ::bd::note_launch();
+    fine_reduce<1>(h, x, fp, r, make_fin(h, 6, 0, cond), s);
     BD_LAUNCH_CHECK();
     BD_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
     cudaGraphNodeParams np = {};
@@ -1163,21 +1263,17 @@ static int capture_graph(amg_hierarchy *h)
     const long long c1 = launch_count();
     BD_CUDA(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     BD_TRY(vcycle_device(h, (const double *)r, (double *)z, s2));
-    k_z_stats<<<G, 256, 0, s2>>>(N, z, r, zold, part); ::bd::note_launch();
-    k_finish<<<1, 1024, 0, s2>>>(part, G, scal, 3, N, -1, flex, 0); ::bd::note_launch();
-    k_p_update<<<G, 256, 0, s2>>>(N, z, p, zold, scal, -1); ::bd::note_launch();
-    fine_reduce<0>(h, p, nullptr, q, part, s2);
-    k_finish<<<1, 1024, 0, s2>>>(part, G, scal, 4, N, 0, flex, 0); ::bd::note_launch();
-    k_xr_update<<<G, 256, 0, s2>>>(N, x, r, p, q, scal, part); ::bd::note_launch();
-    k_finish<<<1, 1024, 0, s2>>>(part, G, scal, 7, N, 0, flex, cond); ::bd::note_launch();
+    k_z_stats<<<G, 256, 0, s2>>>(N, z, r, zold, make_fin(h, 3, -1)); ::bd::note_launch();
+    p_update(h, N, z, p, zold, scal, -1, s2);
+    fine_reduce<0>(h, p, nullptr, q, make_fin(h, 4, 0), s2);
+    xr_update(h, N, x, r, p, q, make_fin(h, 7, 0, cond), s2);
     BD_LAUNCH_CHECK();
     cudaGraph_t body_out = nullptr;
     BD_CUDA(cudaStreamEndCapture(s2, &body_out));
     const long long c2 = launch_count();
     BD_CUDA(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
     k_zero_if<<<G, 256, 0, s>>>(N, x, scal, 1); ::bd::note_launch();
-    fine_reduce<1>(h, x, fp, nullptr, part, s);
-    k_finish<<<1, 1024, 0, s>>>(part, G, scal, 5, N, 0, flex, 0); ::bd::note_launch();
+    fine_reduce<1>(h, x, fp, nullptr, make_fin(h, 5, 0), s);
     k_project_x<<<G, 256, 0, s>>>(N, x, scal); ::bd::note_launch();
     BD_LAUNCH_CHECK();
     const long long c3 = launch_count();
