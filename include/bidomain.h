@@ -253,6 +253,50 @@ int bd_sim_get_state(const bd_sim *s, double *v, double *ue, double *w, int on_d
 int bd_step(bd_sim *s, int nsteps, const solve_options *opts, void *stream, solve_info *last);
 void bd_sim_destroy(bd_sim *s);
 
+/* ---- serving: continuous batching of simulations ---------------------------
+ * A request is a whole simulation (slab, fibre table, stimulus, number of time
+ * steps, as for bd_assemble / bd_sim_create; host arrays, copied at submit).
+ * Each tick of the scheduler (1) admits queued requests in arrival order while
+ * the estimated device-memory footprint of the resident requests stays within
+ * hbm_budget (estimate from the measured bytes per node of earlier requests;
+ * a request that alone exceeds the budget fails with BD_ENOMEM), builds their
+ * operator and hierarchy, which stay resident until the request finishes;
+ * (2) enqueues one time step of every admitted simulation, each on its own
+ * stream, so solves of different sizes overlap on the GPU; (3) waits for them
+ * and retires finished requests, whose memory admits the next ones.  A
+ * request's result does not depend on the other requests in flight (every
+ * request owns its buffers; the kernels are deterministic).  Times are host
+ * milliseconds since bd_server_create.  Not thread-safe: one host thread
+ * drives a server. */
+typedef struct bd_server bd_server;
+typedef struct {
+    long long hbm_budget; /* bytes the resident requests may hold (0: 80 % of free memory) */
+    int max_active;       /* simulations advanced per tick (16)                     */
+    int precision;        /* V-cycle precision of every request (0: FP64, 1: FP32)  */
+    double rtol;          /* (1e-8)                                                 */
+    int max_it;           /* (500)                                                  */
+} bd_server_options;
+typedef struct {
+    int state;            /* 0 queued, 1 active, 2 done, < 0 failed with that status */
+    int steps_done;
+    long long total_iters;
+    double submit_ms, admit_ms, done_ms;
+    long long footprint;  /* measured device bytes while resident (0 when not)       */
+    int n_nodes;
+} bd_request_info;
+void bd_server_options_default(bd_server_options *o);
+int bd_server_create(const bd_server_options *opts, bd_server **out);
+int bd_server_submit(bd_server *s, const bd_mesh *mesh, const bd_params *params, const double *fib,
+                     const double *stim, double stim_ms, int nsteps, long long *id);
+int bd_server_tick(bd_server *s, int *n_active, int *n_queued);
+int bd_server_drain(bd_server *s); /* tick until nothing is queued or active */
+int bd_server_request(const bd_server *s, long long id, bd_request_info *out);
+/* final (v, u_e, w) of a finished request into host arrays of n_nodes doubles */
+int bd_server_result(const bd_server *s, long long id, double *v, double *ue, double *w);
+int bd_server_stats(const bd_server *s, long long *solves, long long *resident_bytes,
+                    long long *budget_bytes);
+void bd_server_destroy(bd_server *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,7 @@ UNITS = {
     "amg_setup.cu": ["-fmad=false"],
     "amg_solve.cu": [],
     "bd_step.cu": [],
+    "bd_serve.cu": [],
 }
 
 

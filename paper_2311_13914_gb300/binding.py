@@ -73,6 +73,20 @@ class KernelProfile(C.Structure):
                 ("flops", C.c_double), ("precision", C.c_int)]
 
 
+class ServerOptions(C.Structure):
+    _fields_ = [("hbm_budget", C.c_longlong), ("max_active", C.c_int), ("precision", C.c_int),
+                ("rtol", C.c_double), ("max_it", C.c_int)]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("state", C.c_int), ("steps_done", C.c_int), ("total_iters", C.c_longlong),
+                ("submit_ms", C.c_double), ("admit_ms", C.c_double), ("done_ms", C.c_double),
+                ("footprint", C.c_longlong), ("n_nodes", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class RmParams(C.Structure):
     _fields_ = [("G", C.c_double), ("vth", C.c_double), ("vp", C.c_double),
                 ("eta1", C.c_double), ("eta2", C.c_double), ("eta3", C.c_double)]
@@ -86,6 +100,9 @@ EXPORTS = (
     "amg_setup", "amg_setup_from_csr", "amg_num_levels", "amg_level_info", "amg_export_level",
     "amg_vcycle", "amg_solve", "amg_destroy", "amg_profile_enable", "amg_profile_read",
     "bd_sim_create", "bd_sim_set_state", "bd_sim_get_state", "bd_step", "bd_sim_destroy",
+    "bd_server_options_default", "bd_server_create", "bd_server_submit", "bd_server_tick",
+    "bd_server_drain", "bd_server_request", "bd_server_result", "bd_server_stats",
+    "bd_server_destroy",
 )
 
 _lock = threading.Lock()
@@ -140,6 +157,18 @@ def lib():
             L.bd_step.argtypes = [_vp, C.c_int, _P(SolveOptions), _vp, _P(SolveInfo)]
             L.bd_sim_destroy.argtypes = [_vp]
             L.bd_sim_destroy.restype = None
+            L.bd_server_options_default.argtypes = [_P(ServerOptions)]
+            L.bd_server_options_default.restype = None
+            L.bd_server_create.argtypes = [_P(ServerOptions), _P(_vp)]
+            L.bd_server_submit.argtypes = [_vp, _P(Mesh), _P(Params), _vp, _vp, C.c_double, C.c_int,
+                                           _P(C.c_longlong)]
+            L.bd_server_tick.argtypes = [_vp, _P(C.c_int), _P(C.c_int)]
+            L.bd_server_drain.argtypes = [_vp]
+            L.bd_server_request.argtypes = [_vp, C.c_longlong, _P(RequestInfo)]
+            L.bd_server_result.argtypes = [_vp, C.c_longlong, _vp, _vp, _vp]
+            L.bd_server_stats.argtypes = [_vp, _P(C.c_longlong), _P(C.c_longlong), _P(C.c_longlong)]
+            L.bd_server_destroy.argtypes = [_vp]
+            L.bd_server_destroy.restype = None
             _lib = L
     return _lib
 
@@ -436,3 +465,67 @@ def bd_step(sim: Sim, nsteps: int, opts: SolveOptions | None = None, stream=None
     if raise_on_error and st != BD_OK:
         raise BidomainError(st, "bd_step")
     return info.as_dict()
+
+
+# ------------------------------------------------------------------ serving
+class Server(_Handle):
+    _destroy = "bd_server_destroy"
+
+
+def bd_server_options_default(**over) -> ServerOptions:
+    o = ServerOptions()
+    lib().bd_server_options_default(C.byref(o))
+    for k, v in over.items():
+        setattr(o, k, v)
+    return o
+
+
+def bd_server_create(opts: ServerOptions | None = None) -> Server:
+    out = _vp()
+    o = opts if opts is not None else bd_server_options_default()
+    _check(lib().bd_server_create(C.byref(o), C.byref(out)), "bd_server_create")
+    return Server(out)
+
+
+def bd_server_submit(srv: Server, mesh: dict, params: dict, fib, stim=None, stim_ms: float = 0.0,
+                     nsteps: int = 1) -> int:
+    m = Mesh(mesh["nx"], mesh["ny"], mesh["nz"], mesh["lx"], mesh["ly"], mesh["lz"])
+    p = Params(params["chi"], params["cm"], params["dt"], params["sil"], params["sit"],
+               params["sel"], params["set"])
+    f = np.ascontiguousarray(fib, dtype=np.float64).reshape(-1)
+    st_ = None if stim is None else np.ascontiguousarray(stim, dtype=np.float64)
+    rid = C.c_longlong()
+    _check(lib().bd_server_submit(srv.ptr, C.byref(m), C.byref(p), f.ctypes.data_as(_vp),
+                                  None if st_ is None else st_.ctypes.data_as(_vp), stim_ms, nsteps,
+                                  C.byref(rid)), "bd_server_submit")
+    return rid.value
+
+
+def bd_server_tick(srv: Server):
+    a, q = C.c_int(), C.c_int()
+    _check(lib().bd_server_tick(srv.ptr, C.byref(a), C.byref(q)), "bd_server_tick")
+    return a.value, q.value
+
+
+def bd_server_drain(srv: Server):
+    _check(lib().bd_server_drain(srv.ptr), "bd_server_drain")
+
+
+def bd_server_request(srv: Server, rid: int) -> dict:
+    r = RequestInfo()
+    _check(lib().bd_server_request(srv.ptr, rid, C.byref(r)), "bd_server_request")
+    return r.as_dict()
+
+
+def bd_server_result(srv: Server, rid: int):
+    n = bd_server_request(srv, rid)["n_nodes"]
+    v, ue, w = np.zeros(n), np.zeros(n), np.zeros(n)
+    _check(lib().bd_server_result(srv.ptr, rid, v.ctypes.data_as(_vp), ue.ctypes.data_as(_vp),
+                                  w.ctypes.data_as(_vp)), "bd_server_result")
+    return v, ue, w
+
+
+def bd_server_stats(srv: Server) -> dict:
+    a, b, c = C.c_longlong(), C.c_longlong(), C.c_longlong()
+    _check(lib().bd_server_stats(srv.ptr, C.byref(a), C.byref(b), C.byref(c)), "bd_server_stats")
+    return dict(solves=a.value, resident_bytes=b.value, budget_bytes=c.value)

@@ -65,6 +65,7 @@ struct amg_hierarchy {
     bool graph_failed = false;
     long long graph_pre = 0, graph_body = 0, graph_post = 0;  // kernel nodes per section
     double *host_init = nullptr;  // pinned initial scalar block for a graph launch
+    cudaEvent_t ev_solve[2] = {nullptr, nullptr};  // device time of a graph-form solve
     bd::DBuf<double> partial;   // kRedBlocks x 4 partial sums
     bd::DBuf<unsigned int> counter;  // arrival counter of the last-block reductions
     bd::DBuf<double> scal;      // device scalars of the PCG recurrences
@@ -83,6 +84,8 @@ struct amg_hierarchy {
         if (cap_stream) cudaStreamDestroy(cap_stream);
         if (cap_stream2) cudaStreamDestroy(cap_stream2);
         if (host_init) cudaFreeHost(host_init);
+        if (ev_solve[0]) cudaEventDestroy(ev_solve[0]);
+        if (ev_solve[1]) cudaEventDestroy(ev_solve[1]);
     }
 };
 
@@ -92,6 +95,9 @@ int pcg_solve_device(amg_hierarchy *h, const double *f_dev, double *x_dev, int w
                      const solve_options *o, cudaStream_t s, solve_info *info);
 int vcycle_device(amg_hierarchy *h, const double *r_dev, double *z_dev, cudaStream_t s);
 int prepare_solve(amg_hierarchy *h);
+int pcg_solve_begin(amg_hierarchy *h, const double *f_dev, double *x_dev, int warm,
+                    const solve_options *o, cudaStream_t s, solve_info *info, bool *pending);
+int pcg_solve_end(amg_hierarchy *h, cudaStream_t s, solve_info *info);
 int build_fine_sell(amg_hierarchy *h, const bd_system *sys, cudaStream_t s);
 int prof_begin(amg_hierarchy *h, cudaStream_t s);
 void prof_end(amg_hierarchy *h, int slot, double bytes, double flops, cudaStream_t s);

@@ -1302,14 +1302,18 @@ static int build_graph(amg_hierarchy *h)
     return st;
 }
 
-static int pcg_solve_graph(amg_hierarchy *h, const double *f_dev, double *x_dev, int warm,
-                           const solve_options *o, cudaStream_t s, solve_info *info)
+// Enqueue one graph-form solve on `s` (inputs copied in, the graph, the
+// iterate copied out, the device scalars copied to the pinned host block);
+// pcg_graph_finish waits for it.  Only one solve per hierarchy may be in flight.
+static int pcg_graph_launch(amg_hierarchy *h, const double *f_dev, double *x_dev, int warm,
+                            const solve_options *o, cudaStream_t s)
 {
     const size_t bytes = sizeof(double) * 2 * (size_t)h->lev[0].N;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    BD_CUDA(cudaEventCreate(&e0));
-    BD_CUDA(cudaEventCreate(&e1));
-    BD_CUDA(cudaEventRecord(e0, s));
+    if (!h->ev_solve[0]) {
+        BD_CUDA(cudaEventCreate(&h->ev_solve[0]));
+        BD_CUDA(cudaEventCreate(&h->ev_solve[1]));
+    }
+    BD_CUDA(cudaEventRecord(h->ev_solve[0], s));
     if (f_dev != h->fin.p) BD_CUDA(cudaMemcpyAsync(h->fin.p, f_dev, bytes, cudaMemcpyDeviceToDevice, s));
     if (warm && x_dev != h->x.p) BD_CUDA(cudaMemcpyAsync(h->x.p, x_dev, bytes, cudaMemcpyDeviceToDevice, s));
     for (int i = 0; i < S_NSLOTS; i++) h->host_init[i] = 0.0;
@@ -1319,12 +1323,16 @@ static int pcg_solve_graph(amg_hierarchy *h, const double *f_dev, double *x_dev,
     BD_CUDA(cudaMemcpyAsync(h->scal.p, h->host_init, sizeof(double) * S_NSLOTS, cudaMemcpyHostToDevice, s));
     BD_CUDA(cudaGraphLaunch(h->graph_exec, s));
     if (x_dev != h->x.p) BD_CUDA(cudaMemcpyAsync(x_dev, h->x.p, bytes, cudaMemcpyDeviceToDevice, s));
-    BD_CUDA(cudaEventRecord(e1, s));
-    BD_TRY(read_scal(h, s));
+    BD_CUDA(cudaEventRecord(h->ev_solve[1], s));
+    BD_CUDA(cudaMemcpyAsync(h->host_scal, h->scal.p, sizeof(double) * S_NSLOTS, cudaMemcpyDeviceToHost, s));
+    return BD_OK;
+}
+
+static int pcg_graph_finish(amg_hierarchy *h, cudaStream_t s, solve_info *info)
+{
+    BD_CUDA(cudaStreamSynchronize(s));
     float ms = 0.0f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    cudaEventElapsedTime(&ms, h->ev_solve[0], h->ev_solve[1]);
     const double *sc = h->host_scal;
     const double nf = sqrt(sc[S_NF2]);
     const int status = (int)sc[S_STATUS];
@@ -1339,20 +1347,47 @@ static int pcg_solve_graph(amg_hierarchy *h, const double *f_dev, double *x_dev,
     return status;
 }
 
+static int pcg_solve_graph(amg_hierarchy *h, const double *f_dev, double *x_dev, int warm,
+                           const solve_options *o, cudaStream_t s, solve_info *info)
+{
+    BD_TRY(pcg_graph_launch(h, f_dev, x_dev, warm, o, s));
+    return pcg_graph_finish(h, s, info);
+}
+
+static bool graph_form(amg_hierarchy *h, const solve_options *o)
+{
+    static const bool graph_off = [] {
+        const char *e = getenv("BD_SOLVE_GRAPH");
+        return e && e[0] == '0';
+    }();
+    if (h->prof || o->strict || h->graph_failed || graph_off) return false;
+    if (!h->graph_exec && build_graph(h) != BD_OK) h->graph_failed = true;
+    return h->graph_exec != nullptr;
+}
+
+// Split form for callers that overlap several hierarchies' solves: begin
+// enqueues the solve (graph form) or runs it to completion (host-driven loop),
+// end waits and reports.
+int pcg_solve_begin(amg_hierarchy *h, const double *f_dev, double *x_dev, int warm,
+                    const solve_options *o, cudaStream_t s, solve_info *info, bool *pending)
+{
+    if (graph_form(h, o)) {
+        *pending = true;
+        return pcg_graph_launch(h, f_dev, x_dev, warm, o, s);
+    }
+    *pending = false;
+    return pcg_solve_loop(h, f_dev, x_dev, warm, o, s, info);
+}
+
+int pcg_solve_end(amg_hierarchy *h, cudaStream_t s, solve_info *info) { return pcg_graph_finish(h, s, info); }
+
 // The graph form unless live kernel timing is on (its CUDA events bracket
 // single launches), strict mode is requested (checked on the host before the
 // loop), the graph could not be built, or BD_SOLVE_GRAPH=0 is set.
 int pcg_solve_device(amg_hierarchy *h, const double *f_dev, double *x_dev, int warm,
                      const solve_options *o, cudaStream_t s, solve_info *info)
 {
-    static const bool graph_off = [] {
-        const char *e = getenv("BD_SOLVE_GRAPH");
-        return e && e[0] == '0';
-    }();
-    if (!h->prof && !o->strict && !h->graph_failed && !graph_off) {
-        if (!h->graph_exec && build_graph(h) != BD_OK) h->graph_failed = true;
-        if (h->graph_exec) return pcg_solve_graph(h, f_dev, x_dev, warm, o, s, info);
-    }
+    if (graph_form(h, o)) return pcg_solve_graph(h, f_dev, x_dev, warm, o, s, info);
     return pcg_solve_loop(h, f_dev, x_dev, warm, o, s, info);
 }
 

@@ -57,6 +57,29 @@ __global__ void k_deinterleave(int N, const double2 *__restrict__ x, double *__r
     }
 }
 
+// One time step split in two for callers that overlap several simulations:
+// begin fuses the membrane update and right-hand side, then enqueues the
+// warm-started solve; end waits for it and advances the step counter.
+int sim_step_begin(bd_sim *sim, const solve_options *o, cudaStream_t s, solve_info *info,
+                   bool *pending)
+{
+    const bd_params &P = sim->sys->params;
+    const double t = (double)sim->step * P.dt;
+    const int on = t < sim->stim_ms;
+    k_rm_rhs<<<grid_for(sim->N, 256), 256, 0, s>>>(sim->N, (double2 *)sim->x.p, sim->w.p,
+                                                   sim->sys->M.p, sim->stim.p, on, P.chi, P.cm,
+                                                   P.dt, sim->rm, (double2 *)sim->f.p); ::bd::note_launch();
+    BD_LAUNCH_CHECK();
+    return pcg_solve_begin(sim->h, sim->f.p, sim->x.p, 1, o, s, info, pending);
+}
+
+int sim_step_end(bd_sim *sim, cudaStream_t s, solve_info *info, bool pending)
+{
+    int st = pending ? pcg_solve_end(sim->h, s, info) : info->status;
+    sim->step++;
+    return st;
+}
+
 }  // namespace bd
 
 using namespace bd;
@@ -184,16 +207,12 @@ extern "C" int bd_step(bd_sim *sim, int nsteps, const solve_options *opts, void 
     long long total = 0;
     solve_info info{};
     int st = BD_OK;
+    (void)P;
     for (int k = 0; k < nsteps; k++) {
-        double t = (double)sim->step * P.dt;
-        int on = t < sim->stim_ms;
-        k_rm_rhs<<<grid_for(sim->N, 256), 256, 0, s>>>(sim->N, (double2 *)sim->x.p, sim->w.p,
-                                                       sim->sys->M.p, sim->stim.p, on, P.chi, P.cm,
-                                                       P.dt, sim->rm, (double2 *)sim->f.p); ::bd::note_launch();
-        BD_LAUNCH_CHECK();
-        st = pcg_solve_device(sim->h, sim->f.p, sim->x.p, 1, &o, s, &info);
+        bool pending = false;
+        st = sim_step_begin(sim, &o, s, &info, &pending);
+        if (st == BD_OK || !pending) st = sim_step_end(sim, s, &info, pending);
         total += info.iters;
-        sim->step++;
         if (st != BD_OK) break;
     }
     info.total_iters = total;
