@@ -261,9 +261,11 @@ void bd_sim_destroy(bd_sim *s);
  * hbm_budget (estimate from the measured bytes per node of earlier requests;
  * a request that alone exceeds the budget fails with BD_ENOMEM), builds their
  * operator and hierarchy, which stay resident until the request finishes;
- * (2) enqueues one time step of every admitted simulation, each on its own
- * stream, so solves of different sizes overlap on the GPU; (3) waits for them
- * and retires finished requests, whose memory admits the next ones.  A
+ * (2) starts a time step of every idle admitted simulation, each on its own
+ * stream, so solves of different sizes overlap on the GPU; (3) waits until at
+ * least one started step has finished, starts the next step of each request
+ * whose step finished (small simulations advance while large ones solve) and
+ * retires finished requests, whose memory admits the next ones.  A
  * request's result does not depend on the other requests in flight (every
  * request owns its buffers; the kernels are deterministic).  Times are host
  * milliseconds since bd_server_create.  Not thread-safe: one host thread

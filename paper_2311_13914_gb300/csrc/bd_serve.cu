@@ -6,15 +6,17 @@
 // admitted request's operator, hierarchy and state resident until its last
 // step, and on every tick advances all admitted simulations by one time step:
 // the steps are enqueued on one stream per request (each a whole-solve CUDA
-// graph), so solves of different sizes overlap on the GPU, and only then
-// waited for.  Finished requests release their memory, which lets the next
-// queued requests in.  Results do not depend on what else is running: every
+// graph), so solves of different sizes overlap on the GPU; a request whose
+// step has finished gets its next step enqueued at once, so small
+// simulations advance while large ones are still solving.  Finished requests
+// release their memory, which lets the next queued requests in.  Results do not depend on what else is running: every
 // request owns its buffers and the kernels are deterministic.
 #include <algorithm>
 #include <chrono>
 #include <deque>
 #include <map>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "amg_internal.cuh"
@@ -42,7 +44,8 @@ struct Request {
     amg_hierarchy *h = nullptr;
     bd_sim *sim = nullptr;
     cudaStream_t stream = nullptr;
-    bool pending = false;
+    bool pending = false;   // a graph-form step is enqueued
+    bool inflight = false;  // a step has been started and not yet completed
     solve_info info{};
     std::vector<double> v, ue, w;
 
@@ -208,34 +211,64 @@ extern "C" int bd_server_tick(bd_server *S, int *n_active, int *n_queued)
         }
         S->active.push_back(r.id);
     }
-    // 2. enqueue one time step of every admitted simulation, each on its stream
+    // 2. start a step of every admitted simulation that is idle, each on its stream
     solve_options so;
     solve_options_default(&so);
     so.rtol = S->o.rtol;
     so.max_it = S->o.max_it;
-    for (long long id : S->active) {
-        Request &r = S->reqs[id];
+    auto start = [&](Request &r) {
         r.info = solve_info{};
         int st = bd::sim_step_begin(r.sim, &so, r.stream, &r.info, &r.pending);
         if (st != BD_OK && r.pending) r.pending = false, r.info.status = st;
-    }
-    // 3. wait for each, retire the finished ones
-    std::vector<long long> still;
-    for (long long id : S->active) {
-        Request &r = S->reqs[id];
+        r.inflight = true;
+    };
+    // completes a started step; returns true when the request left the active set
+    auto complete = [&](Request &r) -> bool {
         int st = bd::sim_step_end(r.sim, r.stream, &r.info, r.pending);
+        r.inflight = false;
+        r.pending = false;
         r.iters += r.info.iters;
         r.steps_done++;
         S->solves++;
         if (st != BD_OK) {
             fail(S, r, st);
-        } else if (r.steps_done >= r.nsteps) {
+            return true;
+        }
+        if (r.steps_done >= r.nsteps) {
             retire(S, r);
-        } else {
-            still.push_back(id);
+            return true;
+        }
+        start(r);  // next step right away
+        return false;
+    };
+    for (long long id : S->active) {
+        Request &r = S->reqs[id];
+        if (!r.inflight) start(r);
+    }
+    // 3. wait until at least one started step has completed; complete all that have
+    if (!S->active.empty()) {
+        std::vector<long long> still;
+        bool any = false;
+        for (long long spins = 0;; spins++) {
+            still.clear();
+            for (long long id : S->active) {
+                Request &r = S->reqs[id];
+                const bool ready = !r.pending || cudaStreamQuery(r.stream) != cudaErrorNotReady;
+                if (r.inflight && ready) {
+                    any = true;
+                    if (complete(r)) continue;
+                }
+                still.push_back(id);
+            }
+            S->active.swap(still);
+            if (any || S->active.empty()) break;
+            if (spins < 2000) {
+                std::this_thread::yield();
+            } else {  // long steps: block on the first in-flight stream instead of spinning
+                cudaStreamSynchronize(S->reqs[S->active.front()].stream);
+            }
         }
     }
-    S->active.swap(still);
     if (n_active) *n_active = (int)S->active.size();
     if (n_queued) *n_queued = (int)S->queue.size();
     return BD_OK;
