@@ -74,12 +74,19 @@ typedef struct {
     int max_levels;        /* (10), at most 16                                      */
     int cheb_degree;       /* Chebyshev-Jacobi sweeps per smoothing (2)             */
     int esteig_steps;      /* CG steps of the lambda_max estimate (10), <= 64       */
-    int square_levels;     /* levels whose MIS runs on the squared graph (1)        */
+    int square_levels;     /* levels whose MIS runs on the squared graph (16: all;
+                              Appendix A squares the first level only, 1)           */
     double eig_lo, eig_hi; /* Chebyshev interval [eig_lo, eig_hi]*lambda (0.05,1.05) */
     unsigned long long seed; /* MIS priorities and Lanczos start vector (0)         */
     int precision;         /* 0: FP64 V-cycle; 1: FP32 V-cycle (values and vectors
                               of every level in FP32, coarsest solve in FP64) inside
                               an FP64 flexible CG (Polak-Ribiere beta) (0)          */
+    int autotune;          /* 0: lanes per block row of the V-cycle's block-CSR
+                              operators from a row-length rule; 1: amg_setup times
+                              every candidate on this GPU and keeps the fastest.
+                              Either way the choice is fixed per hierarchy, so its
+                              solves are reproducible; the two choices differ in
+                              the summation order of row sums (last bits) (0)       */
 } amg_options;
 
 typedef struct {
@@ -189,6 +196,12 @@ int amg_num_levels(const amg_hierarchy *h, int *nlevels);
 int amg_level_info(const amg_hierarchy *h, int level, int *n, long long *nnz, int *n_agg,
                    double *lambda, long long *p_nnz);
 
+/* Lanes per block row the V-cycle uses on level `level` for A_l, R_l and P_l
+ * (lanes[0..2]; 0 where the operator is not applied in block-CSR form: A on a
+ * sliced-ELL finest level, A on the coarsest, R and P on the coarsest).
+ * 64, 128 or 256 mean one thread block of that size per row. */
+int amg_level_lanes(const amg_hierarchy *h, int level, int lanes[3]);
+
 /* Copy level data to HOST arrays (sizes from amg_level_info; any pointer may
  * be NULL): A_l as scalar CSR, MIS flags and aggregate ids per node, P_l as
  * scalar CSR (n rows, 2*n_agg columns).  Synchronises `stream`. */
@@ -219,9 +232,12 @@ void amg_destroy(amg_hierarchy *h);
 /* ---- live timing of the dominant kernel ------------------------------------
  * When enabled, every application of the finest-level operator (the fused
  * SpMV launches of the V-cycle, and of PCG when the V-cycle is FP64) is
- * bracketed by CUDA events on the launching stream; the durations, the algorithmic bytes (matrix values and
- * indices once, each vector stream once) and the flops (2 per scalar nonzero)
- * are summed.  Switching it on resets the sums, switching it off keeps them
+ * bracketed by CUDA events on the launching stream; the durations, the
+ * algorithmic bytes (matrix values and indices once, each vector stream once)
+ * and the flops the kernels execute (an FMA counts 2; the sliced-ELL form of
+ * the finest level needs 2 FMA per stored node pair with its gathered vector
+ * in (v + u, u) form, 2 FMA and an add otherwise, where the 2x2-block operator
+ * would take 8 flops per block) are summed.  Switching it on resets the sums, switching it off keeps them
  * for amg_profile_read; reading requires no pending work.  While it is on,
  * solves run the host-driven loop (one launch at a time) instead of the
  * whole-solve CUDA graph. */

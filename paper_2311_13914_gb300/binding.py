@@ -51,7 +51,7 @@ class AmgOptions(C.Structure):
     _fields_ = [("theta", C.c_double), ("coarse_eq_limit", C.c_int), ("max_levels", C.c_int),
                 ("cheb_degree", C.c_int), ("esteig_steps", C.c_int), ("square_levels", C.c_int),
                 ("eig_lo", C.c_double), ("eig_hi", C.c_double), ("seed", C.c_ulonglong),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("autotune", C.c_int)]
 
 
 class SolveOptions(C.Structure):
@@ -97,7 +97,8 @@ EXPORTS = (
     "bd_strerror", "bd_launch_count", "bd_dot_exact", "bd_dot_exact_noalloc",
     "amg_options_default", "solve_options_default", "bd_rm_params_default",
     "bd_assemble", "bd_system_info", "bd_system_export", "bd_system_destroy",
-    "amg_setup", "amg_setup_from_csr", "amg_num_levels", "amg_level_info", "amg_export_level",
+    "amg_setup", "amg_setup_from_csr", "amg_num_levels", "amg_level_info", "amg_level_lanes",
+    "amg_export_level",
     "amg_vcycle", "amg_solve", "amg_destroy", "amg_profile_enable", "amg_profile_read",
     "bd_sim_create", "bd_sim_set_state", "bd_sim_get_state", "bd_step", "bd_sim_destroy",
     "bd_server_options_default", "bd_server_create", "bd_server_submit", "bd_server_tick",
@@ -143,6 +144,7 @@ def lib():
             L.amg_num_levels.argtypes = [_vp, _P(C.c_int)]
             L.amg_level_info.argtypes = [_vp, C.c_int, _P(C.c_int), _P(C.c_longlong),
                                          _P(C.c_int), _P(C.c_double), _P(C.c_longlong)]
+            L.amg_level_lanes.argtypes = [_vp, C.c_int, _P(C.c_int)]
             L.amg_export_level.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
             L.amg_vcycle.argtypes = [_vp, _vp, _vp, C.c_int, _vp]
             L.amg_solve.argtypes = [_vp, _vp, _vp, C.c_int, _P(SolveOptions), _vp, _P(SolveInfo)]
@@ -357,6 +359,13 @@ def amg_level_info(h: Hierarchy, level: int) -> dict:
     _check(lib().amg_level_info(h.ptr, level, C.byref(n), C.byref(nnz), C.byref(na), C.byref(lam),
                                 C.byref(pn)), "amg_level_info")
     return dict(n=n.value, nnz=nnz.value, n_agg=na.value, lam=lam.value, p_nnz=pn.value)
+
+
+def amg_level_lanes(h: Hierarchy, level: int) -> tuple:
+    """Lanes per block row of A_l, R_l, P_l in the V-cycle (0: not block CSR)."""
+    lanes = (C.c_int * 3)()
+    _check(lib().amg_level_lanes(h.ptr, level, lanes), "amg_level_lanes")
+    return tuple(lanes)
 
 
 def amg_export_level(h: Hierarchy, level: int, stream=None) -> dict:

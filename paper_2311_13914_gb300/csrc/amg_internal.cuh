@@ -26,6 +26,8 @@ struct Level {
     DBuf<float> f32, u32, r32, d32, w32;
     // Chebyshev coefficients (host copies)
     double ch_inv_theta = 0, ch_c1 = 0, ch_c2 = 0;
+    // lanes per block row of A, R and P in the V-cycle's precision
+    int lanes[3] = {0, 0, 0};
 };
 
 // Finest level in sliced-ELL form (32 rows per slice, slot-major), using the
@@ -94,7 +96,7 @@ namespace bd {
 int pcg_solve_device(amg_hierarchy *h, const double *f_dev, double *x_dev, int warm,
                      const solve_options *o, cudaStream_t s, solve_info *info);
 int vcycle_device(amg_hierarchy *h, const double *r_dev, double *z_dev, cudaStream_t s);
-int prepare_solve(amg_hierarchy *h);
+int prepare_solve(amg_hierarchy *h, cudaStream_t s);
 int pcg_solve_begin(amg_hierarchy *h, const double *f_dev, double *x_dev, int warm,
                     const solve_options *o, cudaStream_t s, solve_info *info, bool *pending);
 int pcg_solve_end(amg_hierarchy *h, cudaStream_t s, solve_info *info);

@@ -1215,7 +1215,8 @@ static int check_opts(const amg_options *o)
     if (!(o->theta >= 0.0) || o->coarse_eq_limit < 2 || o->max_levels < 1 ||
         o->max_levels > kMaxLevels || (o->cheb_degree != 1 && o->cheb_degree != 2) ||
         o->esteig_steps < 1 || o->esteig_steps > 64 || o->square_levels < 0 ||
-        !(o->eig_lo > 0.0) || !(o->eig_hi > o->eig_lo) || (o->precision != 0 && o->precision != 1))
+        !(o->eig_lo > 0.0) || !(o->eig_hi > o->eig_lo) || (o->precision != 0 && o->precision != 1) ||
+        (o->autotune != 0 && o->autotune != 1))
         return BD_EINVAL;
     return BD_OK;
 }
@@ -1255,7 +1256,7 @@ extern "C" int amg_setup(const bd_system *sys, const amg_options *opts, void *st
     }
     h->prec32 = o.precision == 1;
     if ((st = setup_from_level0(h, s)) || (st = build_fine_sell(h, sys, s)) ||
-        (st = prepare_solve(h))) {
+        (st = prepare_solve(h, s))) {
         delete h;
         return st;
     }
@@ -1298,7 +1299,7 @@ extern "C" int amg_setup_from_csr(int n, const int *row_ptr, const int *col, con
     h->lev[0].N = n / 2;
     int st = bsr_from_scalar_csr(n, prp, pci, pv, h->lev[0].A, s);
     if (!st) st = setup_from_level0(h, s);
-    if (!st) st = prepare_solve(h);
+    if (!st) st = prepare_solve(h, s);
     if (st) {
         delete h;
         return st;
@@ -1325,6 +1326,17 @@ extern "C" int amg_level_info(const amg_hierarchy *h, int level, int *n, long lo
     if (n_agg) *n_agg = last ? 0 : L.nagg;
     if (lambda) *lambda = last ? 0.0 : L.lam;
     if (p_nnz) *p_nnz = last ? 0 : 4 * L.P.nb;
+    return BD_OK;
+}
+
+extern "C" int amg_level_lanes(const amg_hierarchy *h, int level, int lanes[3])
+{
+    if (!h || !lanes || level < 0 || level >= h->nlev) return BD_EINVAL;
+    const Level &L = h->lev[level];
+    const bool last = level == h->nlev - 1;
+    lanes[0] = last || (level == 0 && h->sell.valid) ? 0 : L.lanes[0];
+    lanes[1] = last ? 0 : L.lanes[1];
+    lanes[2] = last ? 0 : L.lanes[2];
     return BD_OK;
 }
 

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <new>
+#include <type_traits>
 
 #include "amg_internal.cuh"
 
@@ -62,6 +63,7 @@ __global__ void __launch_bounds__(256) k_bsr(int N, const int *__restrict__ rp,
         const bool act = p < N;
         S y0 = 0, y1 = 0;
         const int e = act ? rp[p + 1] : 0;
+#pragma unroll 4
         for (int t = act ? rp[p] + lane : 0; t < e; t += T) {
             const int q = ci[t];
             const BlkS<S> a = load_blk(v, (size_t)t);
@@ -90,6 +92,7 @@ __global__ void __launch_bounds__(TB) k_bsr_wide(int N, const int *__restrict__ 
     for (int p = blockIdx.x; p < N; p += gridDim.x) {
         S y0 = 0, y1 = 0;
         const int e = rp[p + 1];
+#pragma unroll 4
         for (int t = rp[p] + threadIdx.x; t < e; t += TB) {
             const int q = ci[t];
             const BlkS<S> a = load_blk(v, (size_t)t);
@@ -122,18 +125,34 @@ __global__ void __launch_bounds__(TB) k_bsr_wide(int N, const int *__restrict__ 
 }
 
 // ------------------------------------------------------------------ finest level, sliced ELL
+// Block b's share [share_lo(n), share_hi(n)) of n rows or nodes: the grid
+// splits the 32-row slices in equal contiguous parts, so with one resident
+// wave of blocks every SM gets the same work (a grid-stride loop leaves the
+// SMs whose blocks drew one row fewer per thread idle for part of the launch).
+__device__ __forceinline__ int share_lo(int n)
+{
+    return (int)((((long long)n + 31) >> 5) * blockIdx.x / gridDim.x) * 32;
+}
+__device__ __forceinline__ int share_hi(int n)
+{
+    return min(n, (int)((((long long)n + 31) >> 5) * (blockIdx.x + 1) / gridDim.x) * 32);
+}
+
 // One thread per row; slot j of slice s holds entry j of its 32 rows
 // contiguously, so every slot is one coalesced (Ki, Ke) load and one 128-byte
 // column load per warp.  Per node pair: s = v_q + u_q, a += Ki s, b += Ke u_q;
-// then y_v = c M_p v_p + a, y_u = a + b.
-template <class S, class G, class E>
+// then y_v = c M_p v_p + a, y_u = a + b.  SU: the gathered vector is stored as
+// (v + u, u), which saves the add per node pair (two FP64 operations instead
+// of three where the FP64 pipe is the limit).
+template <class S, class G, class E, bool SU = false>
 __global__ void __launch_bounds__(256) k_sell(int N, const int *__restrict__ sptr,
                                                const int *__restrict__ col,
                                                const v2<S> *__restrict__ kk,
                                                const S *__restrict__ cm, G gather, E epi)
 {
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
-        const int sl = p >> 5, lane = p & 31;
+    const int lane = threadIdx.x & 31, e = share_hi(N);
+    for (int p = share_lo(N) + threadIdx.x; p < e; p += blockDim.x) {
+        const int sl = p >> 5;
         const int j1 = sptr[sl + 1];
         S a = 0, b = 0;
 #pragma unroll 4
@@ -142,11 +161,11 @@ __global__ void __launch_bounds__(256) k_sell(int N, const int *__restrict__ spt
             const int q = col[idx];
             const v2<S> k = kk[idx];
             const v2<S> x = gather(q);
-            a = fma(k.x, x.x + x.y, a);
+            a = fma(k.x, SU ? x.x : x.x + x.y, a);
             b = fma(k.y, x.y, b);
         }
         const v2<S> xp = gather(p);
-        epi(p, fma(cm[p], xp.x, a), a + b);
+        epi(p, fma(cm[p], SU ? xp.x - xp.y : xp.x, a), a + b);
     }
 }
 
@@ -156,18 +175,29 @@ template <class S> struct GatherVec {
     __device__ __forceinline__ v2<S> operator()(int q) const { return x[q]; }
 };
 
+// Vectors a finest-level sliced-ELL operator gathers may be kept in the
+// (v + u, u) form (SU); these convert at the epilogue, once per node.
+template <class S, bool SU> __device__ __forceinline__ v2<S> from_su(v2<S> a)
+{
+    return SU ? V2<S>::mk(a.x - a.y, a.y) : a;
+}
+template <class S, bool SU> __device__ __forceinline__ v2<S> to_su(S v, S u)
+{
+    return V2<S>::mk(SU ? v + u : v, u);
+}
+
 // pre-smoothing, degree 2 from zero, d0 = D^{-1} f / theta precomputed:
 // x1 = d0, r1 = f - A d0, d1 = c1 d0 + c2 D^{-1} r1, u = x1 + d1
-template <class S> struct EpiPre {
+template <class S, bool SU = false> struct EpiPre {
     const v2<S> *__restrict__ f;
     const v2<S> *__restrict__ invd;
     const v2<S> *__restrict__ d0;
     v2<S> *__restrict__ u;
     S c1, c2;
     __device__ __forceinline__ void operator()(int p, S y0, S y1) const {
-        const v2<S> fp = f[p], id = invd[p], dp = d0[p];
+        const v2<S> fp = f[p], id = invd[p], dp = from_su<S, SU>(d0[p]);
         const S r0 = fp.x - y0, r1 = fp.y - y1;
-        u[p] = V2<S>::mk(dp.x + (c1 * dp.x + c2 * id.x * r0), dp.y + (c1 * dp.y + c2 * id.y * r1));
+        u[p] = to_su<S, SU>(dp.x + (c1 * dp.x + c2 * id.x * r0), dp.y + (c1 * dp.y + c2 * id.y * r1));
     }
 };
 
@@ -193,16 +223,16 @@ template <class S> struct EpiResid {  // r = f - A u
     }
 };
 
-template <class S> struct EpiAdd {  // u += P e_c
+template <class S, bool SU = false> struct EpiAdd {  // u += P e_c
     v2<S> *__restrict__ u;
     __device__ __forceinline__ void operator()(int p, S y0, S y1) const {
         const v2<S> a = u[p];
-        u[p] = V2<S>::mk(a.x + y0, a.y + y1);
+        u[p] = V2<S>::mk(a.x + (SU ? y0 + y1 : y0), a.y + y1);
     }
 };
 
 // post-smoothing, first half: r0 = f - A u, d0 = D^{-1} r0 / theta, w = u + d0
-template <class S> struct EpiPost1 {
+template <class S, bool SU = false> struct EpiPost1 {
     const v2<S> *__restrict__ f;
     const v2<S> *__restrict__ invd;
     const v2<S> *__restrict__ u;
@@ -211,17 +241,17 @@ template <class S> struct EpiPost1 {
     v2<S> *__restrict__ w;
     S it;
     __device__ __forceinline__ void operator()(int p, S y0, S y1) const {
-        const v2<S> fp = f[p], id = invd[p], up = u[p];
+        const v2<S> fp = f[p], id = invd[p], up = from_su<S, SU>(u[p]);
         const S r0 = fp.x - y0, r1 = fp.y - y1;
         const S d0 = r0 * id.x * it, d1 = r1 * id.y * it;
         r[p] = V2<S>::mk(r0, r1);
-        d[p] = V2<S>::mk(d0, d1);
+        d[p] = to_su<S, SU>(d0, d1);
         w[p] = V2<S>::mk(up.x + d0, up.y + d1);
     }
 };
 
 // post-smoothing, second half: r1 = r0 - A d0, d1 = c1 d0 + c2 D^{-1} r1, u = w + d1
-template <class S> struct EpiPost2 {
+template <class S, bool SU = false> struct EpiPost2 {
     const v2<S> *__restrict__ r;
     const v2<S> *__restrict__ d;
     const v2<S> *__restrict__ invd;
@@ -229,7 +259,7 @@ template <class S> struct EpiPost2 {
     v2<S> *__restrict__ u;
     S c1, c2;
     __device__ __forceinline__ void operator()(int p, S y0, S y1) const {
-        const v2<S> rp_ = r[p], dp = d[p], id = invd[p], wp = w[p];
+        const v2<S> rp_ = r[p], dp = from_su<S, SU>(d[p]), id = invd[p], wp = w[p];
         const S r0 = rp_.x - y0, r1 = rp_.y - y1;
         u[p] = V2<S>::mk(wp.x + (c1 * dp.x + c2 * id.x * r0), wp.y + (c1 * dp.y + c2 * id.y * r1));
     }
@@ -389,19 +419,21 @@ int build_fine_sell(amg_hierarchy *h, const bd_system *sys, cudaStream_t s)
 }
 
 // operator application of level l in precision S: sliced ELL on the finest
-// level when available, 2x2-block CSR otherwise
-template <class S, class G, class E>
+// level when available, 2x2-block CSR otherwise.  SU (sliced ELL only): the
+// gathered vector is in (v + u, u) form.
+template <bool SU = false, class S, class G, class E>
 static int apply_level(amg_hierarchy *h, int l, const LV<S> &lv, G g, E e, cudaStream_t s)
 {
     const Level &L = h->lev[l];
     if (l == 0 && h->sell.valid) {
         const FineSell &F = h->sell;
-        int grid = (int)std::min<long long>(((long long)L.N + 255) / 256, (long long)kSM * 8);
-        k_sell<S><<<grid, 256, 0, s>>>(L.N, F.sptr.p, F.col.p, lv.kk, lv.cm, g, e); ::bd::note_launch();
+        int grid = (int)std::min<long long>(((long long)L.N + 31) / 32, (long long)kSM * 8);
+        k_sell<S, G, E, SU><<<grid, 256, 0, s>>>(L.N, F.sptr.p, F.col.p, lv.kk, lv.cm, g, e); ::bd::note_launch();
         BD_LAUNCH_CHECK();
         return BD_OK;
     }
-    return launch_bsr<S>(L.A, lv.Av, lanes_for(L.A, sizeof(S) == 4), g, e, s);
+    if constexpr (SU) return BD_EINVAL;
+    else return launch_bsr<S>(L.A, lv.Av, L.lanes[0], g, e, s);
 }
 
 // ------------------------------------------------------------------ live kernel timing
@@ -460,7 +492,15 @@ static double fine_bytes(const amg_hierarchy *h, const Level &L, int vec)
                                : (4 * sz + 4.0) * (double)L.A.nb + 4.0 * (L.N + 1);
     return mat + 2 * sz * vec * (double)L.N;
 }
-static double fine_flops(const Level &L) { return 8.0 * (double)L.A.nb; }
+// Flops one finest-level launch executes (an FMA counts 2): sliced ELL 2 FMA
+// per stored slot with the gathered vector in (v + u, u) form, 2 FMA and an
+// add otherwise; block CSR 4 FMA per 2x2 block.  The epilogue's few flops per
+// node are not counted.
+static double fine_flops(const amg_hierarchy *h, const Level &L, bool su)
+{
+    if (h->sell.valid) return (su ? 4.0 : 5.0) * 32.0 * (double)h->sell.slots;
+    return 8.0 * (double)L.A.nb;
+}
 
 // ------------------------------------------------------------------ coarsest level
 // x = Cinv (r - (z.r / z.z) z) in FP64 whatever the storage precision; one
@@ -498,16 +538,16 @@ __global__ void k_coarse_solve(int n, const double *__restrict__ cinv, const dou
 template <class S>
 __global__ void k_copy2(int N, const v2<S> *__restrict__ a, v2<S> *__restrict__ b)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) b[i] = a[i];
+    for (int i = share_lo(N) + threadIdx.x, e = share_hi(N); i < e; i += blockDim.x) b[i] = a[i];
 }
 
-template <class S>
+template <class S, bool SU = false>
 __global__ void k_scale_d0(int N, const v2<S> *__restrict__ f, const v2<S> *__restrict__ invd, S it,
                            v2<S> *__restrict__ d0)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    for (int i = share_lo(N) + threadIdx.x, e = share_hi(N); i < e; i += blockDim.x) {
         const v2<S> a = f[i], b = invd[i];
-        d0[i] = V2<S>::mk(a.x * b.x * it, a.y * b.y * it);
+        d0[i] = to_su<S, SU>(a.x * b.x * it, a.y * b.y * it);
     }
 }
 
@@ -515,7 +555,7 @@ __global__ void k_scale_d0(int N, const v2<S> *__restrict__ f, const v2<S> *__re
 __global__ void k_in32(int N, const double2 *__restrict__ r, const float2 *__restrict__ invd, float it,
                        float2 *__restrict__ f, float2 *__restrict__ d0)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    for (int i = share_lo(N) + threadIdx.x, e = share_hi(N); i < e; i += blockDim.x) {
         const double2 a = r[i];
         const float2 b = invd[i];
         const float f0 = (float)a.x, f1 = (float)a.y;
@@ -526,7 +566,7 @@ __global__ void k_in32(int N, const double2 *__restrict__ r, const float2 *__res
 
 __global__ void k_out64(int N, const float2 *__restrict__ u, double2 *__restrict__ z)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    for (int i = share_lo(N) + threadIdx.x, e = share_hi(N); i < e; i += blockDim.x) {
         const float2 a = u[i];
         z[i] = make_double2((double)a.x, (double)a.y);
     }
@@ -540,13 +580,17 @@ __global__ void k_to_f32(long long n, const double *__restrict__ a, float *__res
 }
 
 // One V-cycle in precision S; f0/u0 are the finest level's right-hand side and
-// output (d0 of the finest level must already be in lev[0]'s d vector).
-template <class S>
+// output (d0 of the finest level must already be in lev[0]'s d vector).  SU0:
+// the finest level's gathered vectors (d0, the iterate u until the last
+// smoothing step, the post-smoother's d) are kept in (v + u, u) form; the
+// output u0 is in (v, u) form either way.
+template <class S, bool SU0>
 static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_t s)
 {
     const int nl = h->nlev;
     const bool deg2 = h->opts.cheb_degree == 2;
-    for (int l = 0; l < nl - 1; l++) {
+    auto down = [&](int l, auto su) -> int {
+        constexpr bool SU = decltype(su)::value;
         Level &L = h->lev[l];
         const LV<S> lv = view<S>(h, l);
         const v2<S> *f = l == 0 ? f0 : lv.f;
@@ -554,21 +598,47 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
         v2<S> *d0 = lv.d;
         if (deg2) {
             int sl = l == 0 ? prof_begin(h, s) : -1;
-            BD_TRY(apply_level<S>(h, l, lv, GatherVec<S>{d0},
-                                  EpiPre<S>{f, lv.invd, d0, u, (S)L.ch_c1, (S)L.ch_c2}, s));
-            prof_end(h, sl, fine_bytes<S>(h, L, 4), fine_flops(L), s);
+            BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{d0},
+                                   EpiPre<S, SU>{f, lv.invd, d0, u, (S)L.ch_c1, (S)L.ch_c2}, s));
+            prof_end(h, sl, fine_bytes<S>(h, L, 4), fine_flops(h, L, SU), s);
         } else {
             k_copy2<S><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, d0, u); ::bd::note_launch();
             BD_LAUNCH_CHECK();
         }
         int sr = l == 0 ? prof_begin(h, s) : -1;
-        BD_TRY(apply_level<S>(h, l, lv, GatherVec<S>{u}, EpiResid<S>{f, lv.r}, s));
-        prof_end(h, sr, fine_bytes<S>(h, L, 3), fine_flops(L), s);
+        BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{u}, EpiResid<S>{f, lv.r}, s));
+        prof_end(h, sr, fine_bytes<S>(h, L, 3), fine_flops(h, L, SU), s);
         const Level &C = h->lev[l + 1];
         const LV<S> cv = view<S>(h, l + 1);
-        BD_TRY(launch_bsr<S>(L.R, lv.Rv, lanes_for(L.R, sizeof(S) == 4), GatherVec<S>{lv.r},
-                             EpiStoreD0<S>{cv.f, cv.d, cv.invd, (S)C.ch_inv_theta}, s));
-    }
+        return launch_bsr<S>(L.R, lv.Rv, L.lanes[1], GatherVec<S>{lv.r},
+                             EpiStoreD0<S>{cv.f, cv.d, cv.invd, (S)C.ch_inv_theta}, s);
+    };
+    auto up = [&](int l, auto su) -> int {
+        constexpr bool SU = decltype(su)::value;
+        Level &L = h->lev[l];
+        const LV<S> lv = view<S>(h, l);
+        const v2<S> *f = l == 0 ? f0 : lv.f;
+        v2<S> *u = l == 0 ? u0 : lv.u;
+        const LV<S> cv = view<S>(h, l + 1);
+        BD_TRY(launch_bsr<S>(L.P, lv.Pv, L.lanes[2], GatherVec<S>{cv.u},
+                             EpiAdd<S, SU>{u}, s));
+        int s1 = l == 0 ? prof_begin(h, s) : -1;
+        BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{u},
+                               EpiPost1<S, SU>{f, lv.invd, u, lv.r, lv.d, lv.w, (S)L.ch_inv_theta}, s));
+        prof_end(h, s1, fine_bytes<S>(h, L, 6), fine_flops(h, L, SU), s);
+        if (deg2) {
+            int s2 = l == 0 ? prof_begin(h, s) : -1;
+            BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{lv.d},
+                                   EpiPost2<S, SU>{lv.r, lv.d, lv.invd, lv.w, u, (S)L.ch_c1, (S)L.ch_c2}, s));
+            prof_end(h, s2, fine_bytes<S>(h, L, 5), fine_flops(h, L, SU), s);
+        } else {
+            k_copy2<S><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, lv.w, u); ::bd::note_launch();
+            BD_LAUNCH_CHECK();
+        }
+        return BD_OK;
+    };
+    for (int l = 0; l < nl - 1; l++)
+        BD_TRY(l == 0 ? down(l, std::integral_constant<bool, SU0>{}) : down(l, std::false_type{}));
     {
         const LV<S> cv = view<S>(h, nl - 1);
         const S *f = (const S *)(nl == 1 ? f0 : cv.f);
@@ -577,27 +647,8 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
         k_coarse_solve<S><<<1, 1024, smem, s>>>(h->nc, h->cinv.p, h->zc.p, h->zz, f, u); ::bd::note_launch();
         BD_LAUNCH_CHECK();
     }
-    for (int l = nl - 2; l >= 0; l--) {
-        Level &L = h->lev[l];
-        const LV<S> lv = view<S>(h, l);
-        const v2<S> *f = l == 0 ? f0 : lv.f;
-        v2<S> *u = l == 0 ? u0 : lv.u;
-        const LV<S> cv = view<S>(h, l + 1);
-        BD_TRY(launch_bsr<S>(L.P, lv.Pv, lanes_for(L.P, sizeof(S) == 4), GatherVec<S>{cv.u}, EpiAdd<S>{u}, s));
-        int s1 = l == 0 ? prof_begin(h, s) : -1;
-        BD_TRY(apply_level<S>(h, l, lv, GatherVec<S>{u},
-                              EpiPost1<S>{f, lv.invd, u, lv.r, lv.d, lv.w, (S)L.ch_inv_theta}, s));
-        prof_end(h, s1, fine_bytes<S>(h, L, 6), fine_flops(L), s);
-        if (deg2) {
-            int s2 = l == 0 ? prof_begin(h, s) : -1;
-            BD_TRY(apply_level<S>(h, l, lv, GatherVec<S>{lv.d},
-                                  EpiPost2<S>{lv.r, lv.d, lv.invd, lv.w, u, (S)L.ch_c1, (S)L.ch_c2}, s));
-            prof_end(h, s2, fine_bytes<S>(h, L, 5), fine_flops(L), s);
-        } else {
-            k_copy2<S><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, lv.w, u); ::bd::note_launch();
-            BD_LAUNCH_CHECK();
-        }
-    }
+    for (int l = nl - 2; l >= 0; l--)
+        BD_TRY(l == 0 ? up(l, std::integral_constant<bool, SU0>{}) : up(l, std::false_type{}));
     return BD_OK;
 }
 
@@ -610,18 +661,26 @@ int vcycle_device(amg_hierarchy *h, const double *r_dev, double *z_dev, cudaStre
         k_in32<<<grid_for(L0.N, 256), 256, 0, s>>>(L0.N, (const double2 *)r_dev, v0.invd,
                                                    (float)L0.ch_inv_theta, v0.f, v0.d); ::bd::note_launch();
         BD_LAUNCH_CHECK();
-        BD_TRY(vcycle_impl<float>(h, v0.f, v0.u, s));
+        BD_TRY((vcycle_impl<float, false>(h, v0.f, v0.u, s)));
         k_out64<<<grid_for(L0.N, 256), 256, 0, s>>>(L0.N, v0.u, (double2 *)z_dev); ::bd::note_launch();
         BD_LAUNCH_CHECK();
         return BD_OK;
     }
+    // FP64 sliced ELL: the finest level's gathered vectors in (v + u, u) form
     const LV<double> v0 = view<double>(h, 0);
+    const bool su = h->sell.valid;
     if (h->nlev > 1) {
-        k_scale_d0<double><<<grid_for(L0.N, 256), 256, 0, s>>>(L0.N, (const double2 *)r_dev, v0.invd,
-                                                               L0.ch_inv_theta, v0.d); ::bd::note_launch();
+        if (su)
+            k_scale_d0<double, true><<<grid_for(L0.N, 256), 256, 0, s>>>(L0.N, (const double2 *)r_dev, v0.invd,
+                                                                         L0.ch_inv_theta, v0.d);
+        else
+            k_scale_d0<double, false><<<grid_for(L0.N, 256), 256, 0, s>>>(L0.N, (const double2 *)r_dev, v0.invd,
+                                                                          L0.ch_inv_theta, v0.d);
+        ::bd::note_launch();
         BD_LAUNCH_CHECK();
     }
-    return vcycle_impl<double>(h, (const double2 *)r_dev, (double2 *)z_dev, s);
+    return su ? vcycle_impl<double, true>(h, (const double2 *)r_dev, (double2 *)z_dev, s)
+              : vcycle_impl<double, false>(h, (const double2 *)r_dev, (double2 *)z_dev, s);
 }
 
 // ------------------------------------------------------------------ PCG reductions
@@ -715,51 +774,44 @@ __device__ void finish_stage(const Fin &f, double a, double b, double c, double 
     }
 }
 
+// Block sums of the first NV of a thread's values, in a fixed order: every
+// thread stores its values, then warp k adds column k (the entries of lanes
+// l, l + 32, ... in index order) and folds its 32 lane sums by shuffles into
+// tot[k].  That is 12 FP64 warp additions per value and block for 256 threads,
+// where a shuffle tree in every warp costs 45.
+template <int NV>
+__device__ __forceinline__ void block_sum(const double (&v)[4], double (*buf)[256], double *tot)
+{
+#pragma unroll
+    for (int k = 0; k < NV; k++) buf[k][threadIdx.x] = v[k];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (w < NV) {
+        double t = buf[w][l];
+        for (int i = l + 32; i < (int)blockDim.x; i += 32) t += buf[w][i];
+        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (l == 0) tot[w] = t;
+    }
+    __syncthreads();
+}
+
 // Block sums -> partial[blockIdx]; the last block to arrive reduces all
 // partials in a fixed order (independent of which block is last, so the
 // result is reproducible) and applies the stage.  No waiting: blocks that are
-// not last simply exit.
-__device__ __forceinline__ void reduce4(double &a, double &b, double &c, double &d, double (*red)[32])
-{
-    for (int o = 16; o; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-        c += __shfl_xor_sync(0xffffffffu, c, o);
-        d += __shfl_xor_sync(0xffffffffu, d, o);
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (l == 0) {
-        red[0][w] = a;
-        red[1][w] = b;
-        red[2][w] = c;
-        red[3][w] = d;
-    }
-    __syncthreads();
-    if (w == 0) {
-        a = l < nw ? red[0][l] : 0.0;
-        b = l < nw ? red[1][l] : 0.0;
-        c = l < nw ? red[2][l] : 0.0;
-        d = l < nw ? red[3][l] : 0.0;
-        for (int o = 16; o; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            b += __shfl_xor_sync(0xffffffffu, b, o);
-            c += __shfl_xor_sync(0xffffffffu, c, o);
-            d += __shfl_xor_sync(0xffffffffu, d, o);
-        }
-    }
-}
-
+// not last simply exit.  NV of (a, b, c, d) are live; the stage sees zeros for
+// the rest.  Needs blockDim.x <= 256 and a multiple of 32.
+template <int NV>
 __device__ void block_finish(double a, double b, double c, double d, const Fin &f)
 {
-    __shared__ double red[kPart][32];
+    __shared__ double buf[NV][256];
+    __shared__ double tot[4];
     __shared__ bool last;
-    reduce4(a, b, c, d, red);
+    double v[4] = {a, b, c, d};
+    block_sum<NV>(v, buf, tot);
     if (threadIdx.x == 0) {
         double *o = f.partial + kPart * blockIdx.x;
-        o[0] = a;
-        o[1] = b;
-        o[2] = c;
-        o[3] = d;
+#pragma unroll
+        for (int k = 0; k < NV; k++) o[k] = tot[k];
         __threadfence();
         const unsigned int ticket = atomicAdd(f.counter, 1u);
         last = ticket == gridDim.x - 1;
@@ -767,18 +819,16 @@ __device__ void block_finish(double a, double b, double c, double d, const Fin &
     __syncthreads();
     if (!last) return;
     __threadfence();
-    a = b = c = d = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) v[k] = 0.0;
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
         const volatile double *q = f.partial + kPart * i;
-        a += q[0];
-        b += q[1];
-        c += q[2];
-        d += q[3];
+#pragma unroll
+        for (int k = 0; k < NV; k++) v[k] += q[k];
     }
-    __syncthreads();
-    reduce4(a, b, c, d, red);
+    block_sum<NV>(v, buf, tot);
     if (threadIdx.x == 0) {
-        finish_stage(f, a, b, c, d);
+        finish_stage(f, tot[0], NV > 1 ? tot[1] : 0.0, NV > 2 ? tot[2] : 0.0, NV > 3 ? tot[3] : 0.0);
         *f.counter = 0u;
     }
 }
@@ -786,30 +836,30 @@ __device__ void block_finish(double a, double b, double c, double d, const Fin &
 __global__ void k_f_stats(int N, const double2 *__restrict__ f, Fin fin)
 {
     double a = 0.0, b = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    for (int i = share_lo(N) + threadIdx.x, e = share_hi(N); i < e; i += blockDim.x) {
         double2 v = f[i];
         a += v.y;
         b += v.x * v.x + v.y * v.y;
     }
-    block_finish(a, b, 0.0, 0.0, fin);
+    block_finish<2>(a, b, 0.0, 0.0, fin);
 }
 
 __global__ void k_project_f(int N, const double2 *__restrict__ f, double2 *__restrict__ fp, Fin fin)
 {
     const double m = fin.scal[S_MEANF];
     double a = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    for (int i = share_lo(N) + threadIdx.x, e = share_hi(N); i < e; i += blockDim.x) {
         double2 v = f[i];
         v.y -= m;
         fp[i] = v;
         a += v.x * v.x + v.y * v.y;
     }
-    block_finish(a, 0.0, 0.0, 0.0, fin);
+    block_finish<1>(a, 0.0, 0.0, 0.0, fin);
 }
 
 __global__ void k_zero2(int N, double2 *x)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+    for (int i = share_lo(N) + threadIdx.x, e = share_hi(N); i < e; i += blockDim.x)
         x[i] = make_double2(0.0, 0.0);
 }
 
@@ -818,7 +868,7 @@ __global__ void k_zero_if(int N, double2 *__restrict__ x, const double *__restri
 {
     const bool z = mode == 0 ? scal[S_WARM] == 0.0 : scal[S_NF2] == 0.0;
     if (!z) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+    for (int i = share_lo(N) + threadIdx.x, e = share_hi(N); i < e; i += blockDim.x)
         x[i] = make_double2(0.0, 0.0);
 }
 
@@ -869,13 +919,13 @@ __global__ void __launch_bounds__(256) k_bsr_reduce(int N, const int *__restrict
             }
         }
     }
-    block_finish(acc, xs, 0.0, 0.0, fin);
+    block_finish<MODE == 0 ? 1 : 2>(acc, xs, 0.0, 0.0, fin);
 }
 
 // Same with the sliced-ELL finest level.  SU: x is stored as (v + u, u), so a
 // node pair costs two FP64 FMAs (a += Ki s, b += Ke u) instead of three.
 template <int MODE, bool SU>
-__global__ void __launch_bounds__(256) k_sell_reduce(int N, const int *__restrict__ sptr,
+__global__ void __launch_bounds__(256, 8) k_sell_reduce(int N, const int *__restrict__ sptr,
                                                       const int *__restrict__ col,
                                                       const double2 *__restrict__ kk,
                                                       const double *__restrict__ cm,
@@ -884,8 +934,9 @@ __global__ void __launch_bounds__(256) k_sell_reduce(int N, const int *__restric
                                                       double2 *__restrict__ out, Fin fin)
 {
     double acc = 0.0, xs = 0.0;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
-        const int sl = p >> 5, lane = p & 31;
+    const int lane = threadIdx.x & 31, e = share_hi(N);
+    for (int p = share_lo(N) + threadIdx.x; p < e; p += blockDim.x) {
+        const int sl = p >> 5;
         const int j1 = sptr[sl + 1];
         double a = 0.0, b = 0.0;
 #pragma unroll 4
@@ -911,7 +962,7 @@ __global__ void __launch_bounds__(256) k_sell_reduce(int N, const int *__restric
             xs += up;
         }
     }
-    block_finish(acc, xs, 0.0, 0.0, fin);
+    block_finish<MODE == 0 ? 1 : 2>(acc, xs, 0.0, 0.0, fin);
 }
 
 // MODE 0 applies A to the search direction (in (v+u, u) form when the finest
@@ -943,7 +994,7 @@ __global__ void k_z_stats(int N, const double2 *__restrict__ z, const double2 *_
                           const double2 *__restrict__ zold, Fin fin)
 {
     double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    for (int i = share_lo(N) + threadIdx.x, e = share_hi(N); i < e; i += blockDim.x) {
         const double2 zi = z[i], ri = r[i];
         a += zi.y;
         b += ri.y;
@@ -953,7 +1004,7 @@ __global__ void k_z_stats(int N, const double2 *__restrict__ z, const double2 *_
             d += ri.x * oi.x + ri.y * oi.y;
         }
     }
-    block_finish(a, b, c, d, fin);
+    block_finish<4>(a, b, c, d, fin);
 }
 
 // z <- z - mean(z_u) e_u; p = z (first iteration) or z + beta p, stored in
@@ -965,7 +1016,7 @@ __global__ void k_p_update(int N, double2 *__restrict__ z, double2 *__restrict__
 {
     const double mz = scal[S_MEANZ], beta = scal[S_BETA];
     if (first < 0) first = scal[S_IT] == 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    for (int i = share_lo(N) + threadIdx.x, e = share_hi(N); i < e; i += blockDim.x) {
         double2 zi = z[i];
         zi.y -= mz;
         z[i] = zi;
@@ -986,7 +1037,7 @@ __global__ void k_xr_update(int N, double2 *__restrict__ x, double2 *__restrict_
 {
     const double alpha = fin.scal[S_ALPHA];
     double acc = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    for (int i = share_lo(N) + threadIdx.x, e = share_hi(N); i < e; i += blockDim.x) {
         double2 xi = x[i], ri = r[i];
         const double2 pi = p[i], qi = q[i];
         const double pv = SU ? pi.x - pi.y : pi.x;
@@ -998,13 +1049,13 @@ __global__ void k_xr_update(int N, double2 *__restrict__ x, double2 *__restrict_
         r[i] = ri;
         acc += ri.x * ri.x + ri.y * ri.y;
     }
-    block_finish(acc, 0.0, 0.0, 0.0, fin);
+    block_finish<1>(acc, 0.0, 0.0, 0.0, fin);
 }
 
 __global__ void k_project_x(int N, double2 *__restrict__ x, const double *__restrict__ scal)
 {
     const double m = scal[S_MEANX];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) x[i].y -= m;
+    for (int i = share_lo(N) + threadIdx.x, e = share_hi(N); i < e; i += blockDim.x) x[i].y -= m;
 }
 
 static void p_update(const amg_hierarchy *h, int N, double2 *z, double2 *p, double2 *zold, double *scal,
@@ -1023,8 +1074,69 @@ static void xr_update(const amg_hierarchy *h, int N, double2 *x, double2 *r, con
     note_launch();
 }
 
+// ------------------------------------------------------------------ lane autotuning
+// Mean time of three launches of one block-CSR operator with T lanes per row
+// (after one untimed launch), with the residual epilogue out = f - M x.
+template <class S>
+static int time_bsr(const BSR &M, const S *vals, int T, const v2<S> *x, const v2<S> *f, v2<S> *out,
+                    cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, float *ms)
+{
+    const EpiResid<S> epi{f, out};
+    BD_TRY(launch_bsr<S>(M, vals, T, GatherVec<S>{x}, epi, s));
+    BD_CUDA(cudaEventRecord(e0, s));
+    for (int k = 0; k < 3; k++) BD_TRY(launch_bsr<S>(M, vals, T, GatherVec<S>{x}, epi, s));
+    BD_CUDA(cudaEventRecord(e1, s));
+    BD_CUDA(cudaEventSynchronize(e1));
+    BD_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    return BD_OK;
+}
+
+// Time every candidate lane count of every block-CSR operator the V-cycle
+// applies (A where the finest level is not sliced ELL, R and P) on this GPU
+// and keep the fastest.  The workspace vectors serve as operands; their
+// contents do not matter.  Lanes change the order of a row's sum, so the
+// choice is fixed per hierarchy: every solve with it is reproducible.
+template <class S>
+static int autotune_lanes(amg_hierarchy *h, cudaStream_t s)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return BD_ECUDA;
+    }
+    int st = BD_OK;
+    for (int l = 0; l < h->nlev - 1 && st == BD_OK; l++) {
+        Level &L = h->lev[l];
+        const LV<S> lv = view<S>(h, l), cv = view<S>(h, l + 1);
+        for (int op = 0; op < 3 && st == BD_OK; op++) {
+            if (op == 0 && l == 0 && h->sell.valid) continue;
+            const BSR &M = op == 0 ? L.A : (op == 1 ? L.R : L.P);
+            const S *vals = op == 0 ? lv.Av : (op == 1 ? lv.Rv : lv.Pv);
+            const v2<S> *x = op == 0 ? lv.u : (op == 1 ? lv.r : cv.u);
+            const v2<S> *f = op == 1 ? cv.f : lv.f;
+            v2<S> *out = op == 0 ? lv.r : (op == 1 ? cv.r : lv.w);
+            const double avg = M.nbr > 0 ? (double)M.nb / M.nbr : 1.0;
+            float best = 0.0f;
+            int bestT = L.lanes[op];
+            for (int T = 1; T <= 256 && st == BD_OK; T <<= 1) {
+                if (T >= 64 && avg < 32.0) break;  // a thread block per short row never wins
+                float ms = 0.0f;
+                st = time_bsr<S>(M, vals, T, x, f, out, s, e0, e1, &ms);
+                if (st == BD_OK && (T == 1 || ms < best)) {
+                    best = ms;
+                    bestT = T;
+                }
+            }
+            L.lanes[op] = bestT;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
 // ------------------------------------------------------------------ workspace
-int prepare_solve(amg_hierarchy *h)
+int prepare_solve(amg_hierarchy *h, cudaStream_t s)
 {
     const bool p32 = h->prec32;
     for (int l = 0; l < h->nlev; l++) {
@@ -1038,13 +1150,13 @@ int prepare_solve(amg_hierarchy *h)
             BD_TRY(L.w32.alloc(n));
             BD_TRY(L.invdiag32.alloc(n));
             BD_TRY(L.A32.alloc(4 * (size_t)L.A.nb));
-            k_to_f32<<<grid_for(n, 256), 256>>>((long long)n, L.invdiag.p, L.invdiag32.p); ::bd::note_launch();
-            k_to_f32<<<grid_for(4 * L.A.nb, 256), 256>>>(4 * L.A.nb, L.A.v.p, L.A32.p); ::bd::note_launch();
+            k_to_f32<<<grid_for(n, 256), 256, 0, s>>>((long long)n, L.invdiag.p, L.invdiag32.p); ::bd::note_launch();
+            k_to_f32<<<grid_for(4 * L.A.nb, 256), 256, 0, s>>>(4 * L.A.nb, L.A.v.p, L.A32.p); ::bd::note_launch();
             if (l < h->nlev - 1) {
                 BD_TRY(L.P32.alloc(4 * (size_t)L.P.nb));
                 BD_TRY(L.R32.alloc(4 * (size_t)L.R.nb));
-                k_to_f32<<<grid_for(4 * L.P.nb, 256), 256>>>(4 * L.P.nb, L.P.v.p, L.P32.p); ::bd::note_launch();
-                k_to_f32<<<grid_for(4 * L.R.nb, 256), 256>>>(4 * L.R.nb, L.R.v.p, L.R32.p); ::bd::note_launch();
+                k_to_f32<<<grid_for(4 * L.P.nb, 256), 256, 0, s>>>(4 * L.P.nb, L.P.v.p, L.P32.p); ::bd::note_launch();
+                k_to_f32<<<grid_for(4 * L.R.nb, 256), 256, 0, s>>>(4 * L.R.nb, L.R.v.p, L.R32.p); ::bd::note_launch();
             }
             BD_LAUNCH_CHECK();
         } else {
@@ -1069,8 +1181,8 @@ int prepare_solve(amg_hierarchy *h)
         size_t nk = 64 * (size_t)F.slots;
         BD_TRY(F.kk32.alloc(nk));
         BD_TRY(F.cm32.alloc((size_t)h->lev[0].N));
-        k_to_f32<<<grid_for(nk, 256), 256>>>((long long)nk, F.kk.p, F.kk32.p); ::bd::note_launch();
-        k_to_f32<<<grid_for(h->lev[0].N, 256), 256>>>(h->lev[0].N, F.cm.p, F.cm32.p); ::bd::note_launch();
+        k_to_f32<<<grid_for(nk, 256), 256, 0, s>>>((long long)nk, F.kk.p, F.kk32.p); ::bd::note_launch();
+        k_to_f32<<<grid_for(h->lev[0].N, 256), 256, 0, s>>>(h->lev[0].N, F.cm.p, F.cm32.p); ::bd::note_launch();
         BD_LAUNCH_CHECK();
     }
     size_t n0 = 2 * (size_t)h->lev[0].N;
@@ -1083,15 +1195,23 @@ int prepare_solve(amg_hierarchy *h)
     BD_TRY(h->fin.alloc(n0));
     if (p32) {
         BD_TRY(h->zold.alloc(n0));
-        BD_CUDA(cudaMemset(h->zold.p, 0, h->zold.bytes()));
+        BD_CUDA(cudaMemsetAsync(h->zold.p, 0, h->zold.bytes(), s));
     }
     BD_TRY(h->partial.alloc(kPart * (size_t)kRedBlocks));
     BD_TRY(h->counter.alloc(1));
-    BD_CUDA(cudaMemset(h->counter.p, 0, sizeof(unsigned int)));
+    BD_CUDA(cudaMemsetAsync(h->counter.p, 0, sizeof(unsigned int), s));
     BD_TRY(h->scal.alloc(S_NSLOTS));
     if (!h->host_scal) BD_CUDA(cudaMallocHost((void **)&h->host_scal, sizeof(double) * S_NSLOTS));
     if (!h->host_init) BD_CUDA(cudaMallocHost((void **)&h->host_init, sizeof(double) * S_NSLOTS));
-    BD_CUDA(cudaDeviceSynchronize());
+    // lanes per block row of the V-cycle's block-CSR operators
+    for (int l = 0; l < h->nlev; l++) {
+        Level &L = h->lev[l];
+        L.lanes[0] = lanes_for(L.A, p32);
+        L.lanes[1] = l < h->nlev - 1 ? lanes_for(L.R, p32) : 0;
+        L.lanes[2] = l < h->nlev - 1 ? lanes_for(L.P, p32) : 0;
+    }
+    if (h->opts.autotune) BD_TRY(p32 ? autotune_lanes<float>(h, s) : autotune_lanes<double>(h, s));
+    BD_CUDA(cudaStreamSynchronize(s));
     return BD_OK;
 }
 
@@ -1164,7 +1284,7 @@ static int pcg_solve_loop(amg_hierarchy *h, const double *f_dev, double *x_dev, 
             p_update(h, N, z, p, zold, scal, it == 0, s);
             int sq = h->prec32 ? -1 : prof_begin(h, s);
             fine_reduce<0>(h, p, nullptr, q, make_fin(h, 4, 0), s);
-            prof_end(h, sq, fine_bytes<double>(h, L0, 2), fine_flops(L0), s);
+            prof_end(h, sq, fine_bytes<double>(h, L0, 2), fine_flops(h, L0, true), s);
             xr_update(h, N, x, r, p, q, make_fin(h, 2, 0), s);
             BD_LAUNCH_CHECK();
             BD_TRY(read_scal(h, s));

@@ -545,6 +545,7 @@ extern "C" void amg_options_default(amg_options *o)
     o->eig_hi = 1.05;
     o->seed = 0;
     o->precision = 0;
+    o->autotune = 0;
 }
 
 extern "C" void solve_options_default(solve_options *o)

@@ -62,6 +62,7 @@ def test_defaults_match_oracle(L, oracle_lib):
               "eig_hi", "seed", "square_levels"):
         assert getattr(o, k) == d[k], k
     assert o.precision == 0  # the plain FP64 form is the default
+    assert o.autotune == 0   # lanes from the row-length rule unless asked
     rm = L.bd_rm_params_default()
     for k, v in oracle_lib.RM_PARAMS.items():
         assert getattr(rm, k) == v

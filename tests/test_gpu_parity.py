@@ -244,6 +244,42 @@ def test_graph_solve_equals_host_loop_solve(B, precision):
         assert ig["true_rel_res"] == il["true_rel_res"]
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotuned_lanes_solve(B, oracle_lib, precision):
+    """amg_options.autotune times the lane counts on the GPU: every chosen
+    count is a valid kernel shape, the V-cycle stays within the V-cycle bound
+    of the oracle (FP64), the solve still meets the oracle's solution, and the
+    graph and loop forms agree bit for bit with the tuned choice."""
+    m = MESHES[3]
+    fib = W.fibre_table(m)
+    sysh = B.bd_assemble(m, W.DEFAULT_PARAMS, fib)
+    h = B.amg_setup(sysh, B.amg_options_default(precision=precision, autotune=1))
+    nl = B.amg_num_levels(h)
+    for l in range(nl):
+        lanes = B.amg_level_lanes(h, l)
+        if l == nl - 1:
+            assert lanes == (0, 0, 0)
+            continue
+        assert lanes[0] == 0 if l == 0 else lanes[0] in (1, 2, 4, 8, 16, 32, 64, 128, 256)
+        assert lanes[1] in (1, 2, 4, 8, 16, 32, 64, 128, 256)
+        assert lanes[2] in (1, 2, 4, 8, 16, 32, 64, 128, 256)
+    o = oracle_lib.assemble(m, W.DEFAULT_PARAMS, fib)
+    H = oracle_lib.Hierarchy(o["A"])
+    f = W.rhs(o["A"].shape[0], seed=7)
+    if precision == 0:
+        r = f.copy()
+        assert np.linalg.norm(B.amg_vcycle(h, r) - H.vcycle(r)) <= 1e-10 * np.linalg.norm(H.vcycle(r))
+    xg, ig = B.amg_solve(h, f)
+    xo, io = H.pcg(f, rtol=1e-8)
+    assert ig["status"] == 0 and ig["true_rel_res"] <= 1e-8 * 1.01
+    assert abs(ig["iters"] - io["iters"]) <= (1 if precision == 0 else 3)
+    assert np.linalg.norm(xg - xo) <= 1e-7 * np.linalg.norm(xo)
+    B.amg_profile_enable(h, True)
+    xl, il = B.amg_solve(h, f)
+    B.amg_profile_enable(h, False)
+    assert il["iters"] == ig["iters"] and np.array_equal(xl, xg)
+
+
 def test_time_stepping_matches_oracle(B, oracle_lib):
     m = W.mesh(16, 16, 8, 0.6, 0.6, 0.3)
     p = W.DEFAULT_PARAMS
