@@ -44,7 +44,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["paper", "small", "profile"], default="paper")
+    ap.add_argument("--workload", choices=["paper", "small", "large", "profile"], default="paper")
     ap.add_argument("--time-steps", type=int, default=T_STEPS)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -57,8 +57,9 @@ def parse_args(argv=None):
     ap.add_argument("--coarse-eq-limit", type=int, default=None)
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
                     help="fp32: FP32 V-cycle inside the FP64 flexible CG")
-    ap.add_argument("--mode", choices=["step", "serve"], default="step",
-                    help="serve: closed-loop capacity and Poisson-load latency of the continuous-batching server")
+    ap.add_argument("--mode", choices=["step", "serve", "batch"], default="step",
+                    help="serve: closed-loop capacity and Poisson-load latency of the continuous-batching "
+                         "server; batch: 64 uneven slabs solved in one graph launch vs one solve at a time")
     ap.add_argument("--requests", type=int, default=16)
     return ap.parse_args(argv)
 
@@ -103,7 +104,7 @@ def workload(name):
 
     # "profile": a 96x96x24 slab whose finest operator (~0.22 GB) still exceeds L2,
     # small enough for full ncu captures
-    mesh = {"paper": W.SLAB_PAPER, "small": W.SLAB_SMALL,
+    mesh = {"paper": W.SLAB_PAPER, "small": W.SLAB_SMALL, "large": W.SLAB_LARGE,
             "profile": W.mesh(96, 96, 24, 1.0, 1.0, 0.5)}[name]
     fib = W.fibre_table(mesh, 120.0, W.fibre_offset_from_seed(1))
     stim = W.stimulus(mesh)
@@ -175,7 +176,7 @@ def source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
+def recorded_traffic(fp32: bool = False):
     """DRAM bytes per finest-level operator launch from the committed ncu
     summary, only while the kernel source is unchanged since the capture."""
     try:
@@ -186,7 +187,7 @@ def recorded_traffic():
                 kv[k.strip()] = v.strip()
         if kv.get("source_digest") != source_digest():
             return None
-        return float(kv["traffic_bytes_per_launch"])
+        return float(kv["traffic_bytes_per_launch_fp32" if fp32 else "traffic_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
         return None
 
@@ -350,7 +351,7 @@ def run_ours(args):
     t_hbm = rec["prof_bytes"] / (hbm_peak * 1e9)
     t_alu = rec["prof_flops"] / alu_peak
     per_launch = rec["prof_bytes"] / rec["prof_launches"] if rec["prof_launches"] else None
-    traffic = recorded_traffic()
+    traffic = recorded_traffic(fp32)
     # the bound is whichever floor is higher for the flops the kernel executes
     # (FP64: 2 DFMA per stored node pair in the (v + u, u) form) and the
     # algorithmic bytes it must move
@@ -363,8 +364,6 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved_gbs / hbm_peak,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"}
-    if fp32:
-        traffic = None  # the committed capture is of the FP64 kernel
     roof.update({"traffic": traffic,
                  "kernel": ("finest-level operator, sliced ELL, FP32 V-cycle (fused epilogues)" if fp32
                             else "finest-level operator, sliced ELL, FP64 (fused epilogues)"),
@@ -591,10 +590,80 @@ def run_serve(args):
                        "max_active": 16}}
 
 
+def run_batch(args):
+    """64 uneven slabs (nx, ny ~ U{16..64}, nz ~ U{8..16}, seed 2), hierarchies
+    resident: every step solves all 64 systems, once as one batched graph
+    launch and once one amg_solve at a time (each its own graph launch)."""
+    import torch
+
+    from paper_2311_13914_gb300 import binding as B
+    from paper_2311_13914_gb300 import workloads as W
+
+    rank, local, world = dist_info()
+    torch.cuda.set_device(local)
+    B.lib()
+    slabs = W.batch_slabs(64, seed=2)
+    stream = torch.cuda.Stream()
+    hs, fs, xs = [], [], []
+    for k, (m, p, fib) in enumerate(slabs):
+        sysh = B.bd_assemble(m, p, fib, stream=stream)
+        h = B.amg_setup(sysh, amg_opts(B, args), stream=stream)
+        n = 2 * W.n_nodes(m)
+        hs.append((sysh, h))
+        fs.append(torch.tensor(W.rhs(n, k), device="cuda"))
+        xs.append(torch.zeros(n, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    b = B.amg_batch_create([h for _, h in hs])
+
+    def sequential():
+        its = 0
+        for (_, h), f, x in zip(hs, fs, xs):
+            its += B.amg_solve(h, f, x, stream=stream)[1]["iters"]
+        return its
+
+    def batched():
+        return sum(i["iters"] for i in B.amg_batch_solve(b, fs, xs, stream=stream))
+
+    for _ in range(max(args.warmup, 1)):
+        sequential()
+        batched()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t = {}
+    its = {}
+    for name, fn in (("sequential", sequential), ("batched", batched)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its[name] = sum(fn() for _ in range(args.steps))
+        torch.cuda.synchronize()
+        t[name] = time.perf_counter() - t0
+    clk = clocks.stop()
+    n_solves = len(slabs) * args.steps
+    rate = {k: n_solves / v for k, v in t.items()}
+    b.close()
+    unknowns = [2 * W.n_nodes(m) for m, _, _ in slabs]
+    return {"metric": "AMG-PCG solves/sec to rtol 1e-8, 64 uneven slabs per step (batched form)",
+            "value": rate["batched"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t["batched"] / args.steps,
+            "higher_is_better": True, "vs_baseline": None,
+            "dtype": "f64 (FP32 V-cycle)" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": f"64 slabs, {min(unknowns)}..{max(unknowns)} unknowns "
+                                   f"({sum(unknowns)} in all), one solve each per step, seed 2",
+                       "batched_solves_per_s": rate["batched"],
+                       "one_at_a_time_solves_per_s": rate["sequential"],
+                       "speedup": rate["batched"] / rate["sequential"],
+                       "mean_pcg_iters": its["batched"] / n_solves,
+                       "amg_options": {k: getattr(amg_opts(B, args), k) for k in
+                                       ("theta", "square_levels", "precision", "autotune")}},
+            "clocks": clk}
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.mode == "serve":
         out = run_serve(args)
+    elif args.mode == "batch":
+        out = run_batch(args)
     else:
         out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:

@@ -229,6 +229,31 @@ int amg_solve(amg_hierarchy *h, const double *f, double *x, int on_device,
 
 void amg_destroy(amg_hierarchy *h);
 
+/* ---- many independent solves in one launch ---------------------------------
+ * The batched form of amg_solve for many small systems (each too small to fill
+ * the GPU on its own): the whole solves of `count` hierarchies (each as in
+ * amg_solve: projected PCG with the V-cycle of Algorithm 2) are captured as
+ * the branches of ONE CUDA graph with no edges between them, so a single
+ * graph launch runs all of them concurrently.  The paper has no counterpart.
+ *
+ * amg_batch_create: h[0..count-1] distinct hierarchies (each one's buffers
+ *   serve one branch; BD_EINVAL on a repeat).  The batch does not own them;
+ *   destroy the batch before any of them, and use none of them elsewhere while
+ *   a batch solve runs.
+ * amg_batch_solve: f[k], x[k]: DEVICE pointers to 2 n_k doubles each (f_k
+ *   right-hand side; x_k initial guess if opts->warm_start, solution out),
+ *   valid on `stream`.  One solve_options for all (strict mode is not
+ *   supported: BD_EINVAL).  info: NULL or count entries (solve_ms is the
+ *   whole batch's device time).  The graph is built on the first call and
+ *   rebuilt when the f/x pointers change.  Synchronises `stream`.  Returns
+ *   BD_OK or the first failing solve's status.  Results equal those of
+ *   amg_solve with the same hierarchy and options bit for bit. */
+typedef struct amg_batch amg_batch;
+int amg_batch_create(amg_hierarchy *const *h, int count, amg_batch **out);
+int amg_batch_solve(amg_batch *b, const double *const *f, double *const *x, const solve_options *opts,
+                    void *stream, solve_info *info);
+void amg_batch_destroy(amg_batch *b);
+
 /* ---- live timing of the dominant kernel ------------------------------------
  * When enabled, every application of the finest-level operator (the fused
  * SpMV launches of the V-cycle, and of PCG when the V-cycle is FP64) is

@@ -99,7 +99,8 @@ EXPORTS = (
     "bd_assemble", "bd_system_info", "bd_system_export", "bd_system_destroy",
     "amg_setup", "amg_setup_from_csr", "amg_num_levels", "amg_level_info", "amg_level_lanes",
     "amg_export_level",
-    "amg_vcycle", "amg_solve", "amg_destroy", "amg_profile_enable", "amg_profile_read",
+    "amg_vcycle", "amg_solve", "amg_destroy", "amg_batch_create", "amg_batch_solve",
+    "amg_batch_destroy", "amg_profile_enable", "amg_profile_read",
     "bd_sim_create", "bd_sim_set_state", "bd_sim_get_state", "bd_step", "bd_sim_destroy",
     "bd_server_options_default", "bd_server_create", "bd_server_submit", "bd_server_tick",
     "bd_server_drain", "bd_server_request", "bd_server_result", "bd_server_stats",
@@ -148,6 +149,10 @@ def lib():
             L.amg_export_level.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
             L.amg_vcycle.argtypes = [_vp, _vp, _vp, C.c_int, _vp]
             L.amg_solve.argtypes = [_vp, _vp, _vp, C.c_int, _P(SolveOptions), _vp, _P(SolveInfo)]
+            L.amg_batch_create.argtypes = [_P(_vp), C.c_int, _P(_vp)]
+            L.amg_batch_solve.argtypes = [_vp, _P(_vp), _P(_vp), _P(SolveOptions), _vp, _P(SolveInfo)]
+            L.amg_batch_destroy.argtypes = [_vp]
+            L.amg_batch_destroy.restype = None
             L.amg_profile_enable.argtypes = [_vp, C.c_int]
             L.amg_profile_read.argtypes = [_vp, _P(KernelProfile)]
             L.amg_destroy.argtypes = [_vp]
@@ -419,6 +424,40 @@ def amg_solve(h: Hierarchy, f, x=None, opts: SolveOptions | None = None, stream=
     if raise_on_error and st not in (BD_OK,):
         raise BidomainError(st, "amg_solve")
     return x, info.as_dict()
+
+
+class Batch(_Handle):
+    _destroy = "amg_batch_destroy"
+
+
+def amg_batch_create(hs) -> Batch:
+    """One CUDA graph over the whole solves of distinct hierarchies hs."""
+    arr = (_vp * len(hs))(*[h.ptr for h in hs])
+    out = _vp()
+    _check(lib().amg_batch_create(arr, len(hs), C.byref(out)), "amg_batch_create")
+    return Batch(out, keep=tuple(hs))
+
+
+def amg_batch_solve(b: Batch, fs, xs, opts: SolveOptions | None = None, stream=None,
+                    raise_on_error: bool = True) -> list:
+    """Solve every system of the batch in one graph launch.  fs, xs: CUDA
+    float64 tensors (x used in place).  Returns the per-solve info dicts."""
+    n = len(fs)
+    if len(xs) != n:
+        raise ValueError("fs and xs differ in length")
+    fp, xp = (_vp * n)(), (_vp * n)()
+    for k in range(n):
+        pf, df, _ = _arr(fs[k], np.float64)
+        px, dx, _ = _arr(xs[k], np.float64)
+        if not (df and dx):
+            raise ValueError("batched solves take CUDA tensors")
+        fp[k], xp[k] = pf, px
+    o = opts if opts is not None else solve_options_default()
+    infos = (SolveInfo * n)()
+    st = lib().amg_batch_solve(b.ptr, fp, xp, C.byref(o), _stream(stream), infos)
+    if raise_on_error and st != BD_OK:
+        raise BidomainError(st, "amg_batch_solve")
+    return [i.as_dict() for i in infos]
 
 
 def amg_profile_enable(h: Hierarchy, enable: bool = True):

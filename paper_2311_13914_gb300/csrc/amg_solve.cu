@@ -1343,12 +1343,15 @@ static void end_capture_quietly(cudaStream_t s)
     cudaGetLastError();
 }
 
-static int capture_graph(amg_hierarchy *h)
+// Capture one whole solve of h into the graph being captured on stream s:
+// pre-loop kernels, a WHILE node whose body (captured on s2) is one PCG
+// iteration and whose condition the device sets, post-loop kernels.  Operates
+// on h's own buffers (f in h->fin, x in h->x, scalars in h->scal).
+static int capture_solve(amg_hierarchy *h, cudaStream_t s, cudaStream_t s2)
 {
     Level &L0 = h->lev[0];
     const int N = L0.N, G = kRedBlocks;
     const bool flex = h->prec32;
-    cudaStream_t s = h->cap_stream, s2 = h->cap_stream2;
     double2 *x = (double2 *)h->x.p, *r = (double2 *)h->r.p, *z = (double2 *)h->z.p;
     double2 *p = (double2 *)h->p.p, *q = (double2 *)h->q.p, *fp = (double2 *)h->fp.p;
     double2 *zold = flex ? (double2 *)h->zold.p : nullptr;
@@ -1357,7 +1360,6 @@ static int capture_graph(amg_hierarchy *h)
     // kernel-node counts per section (the launch counter counts executions, so
     // the increments made while capturing are taken back below)
     const long long c0 = launch_count();
-    BD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     k_f_stats<<<G, 256, 0, s>>>(N, fin, make_fin(h, 0, 0)); ::bd::note_launch();
     k_project_f<<<G, 256, 0, s>>>(N, fin, fp, make_fin(h, 1, 0)); ::bd::note_launch();
     k_zero_if<<<G, 256, 0, s>>>(N, x, scal, 0); ::bd::note_launch();
@@ -1401,7 +1403,14 @@ static int capture_graph(amg_hierarchy *h)
     h->graph_body = c2 - c1;
     h->graph_post = c3 - c2;
     note_launches(-(c3 - c0));
-    BD_CUDA(cudaStreamEndCapture(s, &h->graph));
+    return BD_OK;
+}
+
+static int capture_graph(amg_hierarchy *h)
+{
+    BD_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    BD_TRY(capture_solve(h, h->cap_stream, h->cap_stream2));
+    BD_CUDA(cudaStreamEndCapture(h->cap_stream, &h->graph));
     BD_CUDA(cudaGraphInstantiate(&h->graph_exec, h->graph, 0));
     return BD_OK;
 }
@@ -1425,6 +1434,8 @@ static int build_graph(amg_hierarchy *h)
 // Enqueue one graph-form solve on `s` (inputs copied in, the graph, the
 // iterate copied out, the device scalars copied to the pinned host block);
 // pcg_graph_finish waits for it.  Only one solve per hierarchy may be in flight.
+static int report_from_scal(amg_hierarchy *h, const double *sc, float ms, solve_info *info);
+
 static int pcg_graph_launch(amg_hierarchy *h, const double *f_dev, double *x_dev, int warm,
                             const solve_options *o, cudaStream_t s)
 {
@@ -1453,18 +1464,7 @@ static int pcg_graph_finish(amg_hierarchy *h, cudaStream_t s, solve_info *info)
     BD_CUDA(cudaStreamSynchronize(s));
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, h->ev_solve[0], h->ev_solve[1]);
-    const double *sc = h->host_scal;
-    const double nf = sqrt(sc[S_NF2]);
-    const int status = (int)sc[S_STATUS];
-    note_launches(h->graph_pre + h->graph_post + (long long)sc[S_IT] * h->graph_body);
-    if (info) {
-        info->status = status;
-        info->iters = (int)sc[S_IT];
-        info->rel_res = nf > 0.0 ? sqrt(sc[S_RR]) / nf : 0.0;
-        info->true_rel_res = nf > 0.0 ? sqrt(sc[S_TRR]) / nf : 0.0;
-        info->solve_ms = ms;
-    }
-    return status;
+    return report_from_scal(h, h->host_scal, ms, info);
 }
 
 static int pcg_solve_graph(amg_hierarchy *h, const double *f_dev, double *x_dev, int warm,
@@ -1511,9 +1511,192 @@ int pcg_solve_device(amg_hierarchy *h, const double *f_dev, double *x_dev, int w
     return pcg_solve_loop(h, f_dev, x_dev, warm, o, s, info);
 }
 
+// Report of one solve from its scalar block (graph form): status, iterations,
+// residuals; counts its kernel executions.
+static int report_from_scal(amg_hierarchy *h, const double *sc, float ms, solve_info *info)
+{
+    const double nf = sqrt(sc[S_NF2]);
+    const int status = (int)sc[S_STATUS];
+    note_launches(h->graph_pre + h->graph_post + (long long)sc[S_IT] * h->graph_body);
+    if (info) {
+        info->status = status;
+        info->iters = (int)sc[S_IT];
+        info->rel_res = nf > 0.0 ? sqrt(sc[S_RR]) / nf : 0.0;
+        info->true_rel_res = nf > 0.0 ? sqrt(sc[S_TRR]) / nf : 0.0;
+        info->solve_ms = ms;
+    }
+    return status;
+}
+
+// ------------------------------------------------------------------ batched solves
+// Many independent solves as one CUDA graph: branch k copies f_k and x_k into
+// hierarchy k's buffers, runs its whole solve (capture_solve) and copies x and
+// the scalar block back; the branches have no edges between them, so one
+// launch runs all of them concurrently on the GPU.
+struct BatchGraph {
+    std::vector<amg_hierarchy *> h;
+    std::vector<const double *> f;
+    std::vector<double *> x;
+    std::vector<cudaStream_t> st;
+    std::vector<cudaEvent_t> join;
+    cudaStream_t origin = nullptr, body = nullptr;
+    cudaEvent_t fork = nullptr, ev[2] = {nullptr, nullptr};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    DBuf<double> init_dev;          // count x S_NSLOTS initial scalar blocks
+    double *host_init = nullptr;    // pinned, count x S_NSLOTS
+    double *host_scal = nullptr;    // pinned, count x S_NSLOTS (results)
+
+    void drop_graph()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+    }
+    ~BatchGraph()
+    {
+        drop_graph();
+        for (cudaStream_t q : st) cudaStreamDestroy(q);
+        for (cudaEvent_t e : join) cudaEventDestroy(e);
+        if (origin) cudaStreamDestroy(origin);
+        if (body) cudaStreamDestroy(body);
+        if (fork) cudaEventDestroy(fork);
+        if (ev[0]) cudaEventDestroy(ev[0]);
+        if (ev[1]) cudaEventDestroy(ev[1]);
+        if (host_init) cudaFreeHost(host_init);
+        if (host_scal) cudaFreeHost(host_scal);
+    }
+};
+
+static int batch_capture(BatchGraph &b)
+{
+    const int count = (int)b.h.size();
+    BD_CUDA(cudaStreamBeginCapture(b.origin, cudaStreamCaptureModeThreadLocal));
+    BD_CUDA(cudaEventRecord(b.fork, b.origin));
+    for (int k = 0; k < count; k++) {
+        amg_hierarchy *h = b.h[k];
+        cudaStream_t s = b.st[k];
+        const size_t bytes = sizeof(double) * 2 * (size_t)h->lev[0].N;
+        BD_CUDA(cudaStreamWaitEvent(s, b.fork, 0));
+        BD_CUDA(cudaMemcpyAsync(h->scal.p, b.init_dev.p + (size_t)k * S_NSLOTS, sizeof(double) * S_NSLOTS,
+                                cudaMemcpyDeviceToDevice, s));
+        BD_CUDA(cudaMemcpyAsync(h->fin.p, b.f[k], bytes, cudaMemcpyDeviceToDevice, s));
+        BD_CUDA(cudaMemcpyAsync(h->x.p, b.x[k], bytes, cudaMemcpyDeviceToDevice, s));
+        BD_TRY(capture_solve(h, s, b.body));
+        BD_CUDA(cudaMemcpyAsync(b.x[k], h->x.p, bytes, cudaMemcpyDeviceToDevice, s));
+        BD_CUDA(cudaMemcpyAsync(b.host_scal + (size_t)k * S_NSLOTS, h->scal.p, sizeof(double) * S_NSLOTS,
+                                cudaMemcpyDeviceToHost, s));
+        BD_CUDA(cudaEventRecord(b.join[k], s));
+        BD_CUDA(cudaStreamWaitEvent(b.origin, b.join[k], 0));
+    }
+    BD_CUDA(cudaStreamEndCapture(b.origin, &b.graph));
+    BD_CUDA(cudaGraphInstantiate(&b.exec, b.graph, 0));
+    return BD_OK;
+}
+
 }  // namespace bd
 
 using namespace bd;
+
+struct amg_batch {
+    bd::BatchGraph g;
+};
+
+extern "C" int amg_batch_create(amg_hierarchy *const *h, int count, amg_batch **out)
+{
+    if (!out) return BD_EINVAL;
+    *out = nullptr;
+    if (!h || count < 1) return BD_EINVAL;
+    for (int k = 0; k < count; k++) {
+        if (!h[k]) return BD_EINVAL;
+        for (int j = 0; j < k; j++)
+            if (h[j] == h[k]) return BD_EINVAL;  // one hierarchy's buffers serve one branch
+    }
+    amg_batch *b = new (std::nothrow) amg_batch();
+    if (!b) return BD_ENOMEM;
+    BatchGraph &g = b->g;
+    g.h.assign(h, h + count);
+    int st = BD_OK;
+    auto ok = [&](cudaError_t e) {
+        if (e != cudaSuccess && st == BD_OK) st = BD_ECUDA;
+    };
+    ok(cudaStreamCreateWithFlags(&g.origin, cudaStreamNonBlocking));
+    ok(cudaStreamCreateWithFlags(&g.body, cudaStreamNonBlocking));
+    ok(cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming));
+    ok(cudaEventCreate(&g.ev[0]));
+    ok(cudaEventCreate(&g.ev[1]));
+    g.st.assign(count, nullptr);
+    g.join.assign(count, nullptr);
+    for (int k = 0; k < count && st == BD_OK; k++) {
+        ok(cudaStreamCreateWithFlags(&g.st[k], cudaStreamNonBlocking));
+        ok(cudaEventCreateWithFlags(&g.join[k], cudaEventDisableTiming));
+    }
+    const size_t nsc = (size_t)count * S_NSLOTS;
+    if (st == BD_OK) st = g.init_dev.alloc(nsc);
+    if (st == BD_OK) ok(cudaMallocHost((void **)&g.host_init, sizeof(double) * nsc));
+    if (st == BD_OK) ok(cudaMallocHost((void **)&g.host_scal, sizeof(double) * nsc));
+    if (st != BD_OK) {
+        delete b;
+        return st;
+    }
+    *out = b;
+    return BD_OK;
+}
+
+extern "C" int amg_batch_solve(amg_batch *b, const double *const *f, double *const *x, const solve_options *opts,
+                               void *stream, solve_info *info)
+{
+    if (!b || !f || !x) return BD_EINVAL;
+    BatchGraph &g = b->g;
+    const int count = (int)g.h.size();
+    solve_options o;
+    solve_options_default(&o);
+    if (opts) o = *opts;
+    if (!(o.rtol > 0.0) || o.max_it < 0 || o.strict) return BD_EINVAL;
+    for (int k = 0; k < count; k++)
+        if (!f[k] || !x[k]) return BD_EINVAL;
+    // the graph is tied to the vectors it copies from and to
+    bool same = g.exec != nullptr;
+    for (int k = 0; k < count && same; k++) same = g.f[k] == f[k] && g.x[k] == x[k];
+    if (!same) {
+        g.drop_graph();
+        g.f.assign(f, f + count);
+        g.x.assign(x, x + count);
+        const int st = batch_capture(g);
+        if (st != BD_OK) {
+            end_capture_quietly(g.body);
+            for (cudaStream_t q : g.st) end_capture_quietly(q);
+            end_capture_quietly(g.origin);
+            g.drop_graph();
+            return st;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < count; k++) {
+        double *hi = g.host_init + (size_t)k * S_NSLOTS;
+        for (int i = 0; i < S_NSLOTS; i++) hi[i] = 0.0;
+        hi[S_RTOL] = o.rtol;
+        hi[S_MAXIT] = (double)o.max_it;
+        hi[S_WARM] = o.warm_start ? 1.0 : 0.0;
+    }
+    BD_CUDA(cudaMemcpyAsync(g.init_dev.p, g.host_init, sizeof(double) * count * S_NSLOTS,
+                            cudaMemcpyHostToDevice, s));
+    BD_CUDA(cudaEventRecord(g.ev[0], s));
+    BD_CUDA(cudaGraphLaunch(g.exec, s));
+    BD_CUDA(cudaEventRecord(g.ev[1], s));
+    BD_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, g.ev[0], g.ev[1]);
+    int worst = BD_OK;
+    for (int k = 0; k < count; k++) {
+        const int stk = report_from_scal(g.h[k], g.host_scal + (size_t)k * S_NSLOTS, ms, info ? info + k : nullptr);
+        if (stk != BD_OK && worst == BD_OK) worst = stk;
+    }
+    return worst;
+}
+
+extern "C" void amg_batch_destroy(amg_batch *b) { delete b; }
 
 extern "C" int amg_vcycle(amg_hierarchy *h, const double *r, double *z, int on_device, void *stream)
 {

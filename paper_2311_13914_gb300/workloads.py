@@ -88,3 +88,24 @@ def random_slab(rng: np.random.Generator, lo=(16, 16, 8), hi=(64, 64, 16)):
     rot = float(rng.uniform(60.0, 150.0))
     scale = float(rng.uniform(0.8, 1.2))
     return mesh(nx, ny, nz), rot, scale
+
+
+def batch_slabs(count: int = 64, seed: int = 2) -> list:
+    """Seeded uneven slabs for the batched form: nx, ny ~ U{16..64},
+    nz ~ U{8..16} (cube elements of side 1/24 cm), fibre rotation
+    U[60, 150] degrees with offset U[-30, 30), every conductivity scaled by
+    its own U[0.8, 1.2].  Returns (mesh, params, fibre table) per slab."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        nx, ny = (int(v) for v in rng.integers(16, 65, 2))
+        nz = int(rng.integers(8, 17))
+        rot = float(rng.uniform(60.0, 150.0))
+        off = float(rng.uniform(-30.0, 30.0))
+        sc = rng.uniform(0.8, 1.2, 4)
+        m = mesh(nx, ny, nz)
+        p = dict(DEFAULT_PARAMS)
+        for key, f in zip(("sil", "sit", "sel", "set"), sc):
+            p[key] = DEFAULT_PARAMS[key] * float(f)
+        out.append((m, p, fibre_table(m, rot, off)))
+    return out
