@@ -144,8 +144,8 @@ __device__ __forceinline__ int share_hi(int n)
 // then y_v = c M_p v_p + a, y_u = a + b.  SU: the gathered vector is stored as
 // (v + u, u), which saves the add per node pair (two FP64 operations instead
 // of three where the FP64 pipe is the limit).
-template <class S, class G, class E, bool SU = false>
-__global__ void __launch_bounds__(256) k_sell(int N, const int *__restrict__ sptr,
+template <class S, class G, class E, bool SU = false, int MINB = 8>
+__global__ void __launch_bounds__(256, MINB) k_sell(int N, const int *__restrict__ sptr,
                                                const int *__restrict__ col,
                                                const v2<S> *__restrict__ kk,
                                                const S *__restrict__ cm, G gather, E epi)
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(256) k_sell(int N, const int *__restrict__ spt
         const int sl = p >> 5;
         const int j1 = sptr[sl + 1];
         S a = 0, b = 0;
-#pragma unroll 4
+#pragma unroll (MINB >= 8 ? 4 : 8)
         for (int j = sptr[sl]; j < j1; j++) {
             const size_t idx = (size_t)j * 32 + lane;
             const int q = col[idx];
@@ -427,8 +427,9 @@ static int apply_level(amg_hierarchy *h, int l, const LV<S> &lv, G g, E e, cudaS
     const Level &L = h->lev[l];
     if (l == 0 && h->sell.valid) {
         const FineSell &F = h->sell;
-        int grid = (int)std::min<long long>(((long long)L.N + 31) / 32, (long long)kSM * 8);
-        k_sell<S, G, E, SU><<<grid, 256, 0, s>>>(L.N, F.sptr.p, F.col.p, lv.kk, lv.cm, g, e); ::bd::note_launch();
+        constexpr int MB = sizeof(S) == 8 ? 4 : 8;  // FP64: fewer, deeper-pipelined threads
+        int grid = (int)std::min<long long>(((long long)L.N + 31) / 32, (long long)kSM * MB);
+        k_sell<S, G, E, SU, MB><<<grid, 256, 0, s>>>(L.N, F.sptr.p, F.col.p, lv.kk, lv.cm, g, e); ::bd::note_launch();
         BD_LAUNCH_CHECK();
         return BD_OK;
     }
@@ -925,7 +926,7 @@ __global__ void __launch_bounds__(256) k_bsr_reduce(int N, const int *__restrict
 // Same with the sliced-ELL finest level.  SU: x is stored as (v + u, u), so a
 // node pair costs two FP64 FMAs (a += Ki s, b += Ke u) instead of three.
 template <int MODE, bool SU>
-__global__ void __launch_bounds__(256, 8) k_sell_reduce(int N, const int *__restrict__ sptr,
+__global__ void __launch_bounds__(256, 4) k_sell_reduce(int N, const int *__restrict__ sptr,
                                                       const int *__restrict__ col,
                                                       const double2 *__restrict__ kk,
                                                       const double *__restrict__ cm,
@@ -939,7 +940,7 @@ __global__ void __launch_bounds__(256, 8) k_sell_reduce(int N, const int *__rest
         const int sl = p >> 5;
         const int j1 = sptr[sl + 1];
         double a = 0.0, b = 0.0;
-#pragma unroll 4
+#pragma unroll 8
         for (int j = sptr[sl]; j < j1; j++) {
             const size_t idx = (size_t)j * 32 + lane;
             const int q = col[idx];
@@ -974,7 +975,7 @@ static void fine_reduce(const amg_hierarchy *h, const double2 *x, const double2 
     const Level &L0 = h->lev[0];
     if (h->sell.valid) {
         const FineSell &F = h->sell;
-        k_sell_reduce<MODE, MODE == 0><<<kRedBlocks, 256, 0, s>>>(L0.N, F.sptr.p, F.col.p, (const double2 *)F.kk.p,
+        k_sell_reduce<MODE, MODE == 0><<<kSM * 4, 256, 0, s>>>(L0.N, F.sptr.p, F.col.p, (const double2 *)F.kk.p,
                                                                   F.cm.p, x, f, out, fin); ::bd::note_launch();
         return;
     }
