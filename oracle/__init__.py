@@ -121,6 +121,10 @@ def lib():
             L.oc_pcg.argtypes = [_vp, _vp, _vp, _i, _d, _i, _P(_i), _P(_d), _P(_d)]
             L.oc_bd_step.argtypes = [_vp, _vp, _i, _d, _d, _d, _P(_RM), _vp, _vp, _vp, _vp,
                                      _d, _i, _P(_i)]
+            L.oc_elliptic_block.argtypes = [_P(_CSR), _P(_CSR), _P(_CSR)]
+            L.oc_parabolic_cg.argtypes = [_P(_CSR), _vp, _d, _vp, _vp, _d, _i, _i, _P(_i), _P(_d)]
+            L.oc_bd_step_decoupled.argtypes = [_vp, _P(_CSR), _vp, _i, _d, _d, _d, _P(_RM), _vp,
+                                               _vp, _vp, _vp, _d, _i, _i, _P(_i), _P(_i)]
             _lib = L
     return _lib
 
@@ -284,6 +288,25 @@ def smooth_p(A, Pt, omega: float):
     return _own(out)
 
 
+def elliptic_block(Ki, Ke):
+    """f4: the elliptic operator Ai + Ae as the 2x2-block operator
+    [I, 0; 0, Ai + Ae] on the node pattern (explicit zeros kept)."""
+    a, b, out = _In(Ki), _In(Ke), _CSR()
+    _check(lib().oc_elliptic_block(C.byref(a.s), C.byref(b.s), C.byref(out)), "elliptic_block")
+    return _own(out)
+
+
+def parabolic_cg(Ki, M, c: float, b, v0, rtol=1e-8, max_it=500, jacobi=True):
+    """f4: (c M + Ai) v = b by (Jacobi-preconditioned) CG from v0."""
+    k = _In(Ki)
+    M, b = _f64(M), _f64(b)
+    v = _f64(v0).copy()
+    it, rr = C.c_int(0), C.c_double(0)
+    rc = lib().oc_parabolic_cg(C.byref(k.s), _ptr(M), c, _ptr(b), _ptr(v), rtol, max_it,
+                               int(bool(jacobi)), C.byref(it), C.byref(rr))
+    return v, dict(status=rc, iters=it.value, rel_res=rr.value)
+
+
 def chebyshev(A, f, x0, degree: int, lo: float, hi: float, x_is_zero: bool = False):
     a = _In(A)
     f = _f64(f)
@@ -387,3 +410,19 @@ class Hierarchy:
                               C.byref(crm), _ptr(Iapp), _ptr(v), _ptr(ue), _ptr(w), rtol, max_it,
                               C.byref(it))
         return dict(status=rc, iters=it.value)
+
+    def bd_step_decoupled(self, Ki, M, params: dict, Iapp, v, ue, w, rtol=1e-8, max_it=500,
+                          jacobi=True, rm=None):
+        """f4: one step of the paper's decoupled scheme; self is the hierarchy
+        of elliptic_block(Ki, Ke).  v, ue, w updated in place."""
+        rm = dict(RM_PARAMS if rm is None else rm)
+        k = _In(Ki)
+        M = _f64(M)
+        Iapp = _f64(Iapp)
+        ie, ip = C.c_int(0), C.c_int(0)
+        crm = _RM(rm["G"], rm["vth"], rm["vp"], rm["eta1"], rm["eta2"], rm["eta3"])
+        rc = lib().oc_bd_step_decoupled(self._h, C.byref(k.s), _ptr(M), M.size, params["chi"],
+                                        params["cm"], params["dt"], C.byref(crm), _ptr(Iapp),
+                                        _ptr(v), _ptr(ue), _ptr(w), rtol, max_it, int(bool(jacobi)),
+                                        C.byref(ie), C.byref(ip))
+        return dict(status=rc, iters_elliptic=ie.value, iters_parabolic=ip.value)

@@ -1258,3 +1258,165 @@ int oc_bd_step(const oc_hier *h, const double *M, int N, double chi, double cm,
     free(f); free(x);
     return rc;
 }
+
+/* ======================================================================
+ * f4.  The decoupled scheme the paper runs (Section 2.2, Eqs. 4-7 as
+ * printed): per step the elliptic system with matrix Ai + Ae, then the
+ * parabolic system with matrix c M + Ai, each by its own CG.
+ * ====================================================================== */
+int oc_elliptic_block(const oc_csr *Ki, const oc_csr *Ke, oc_csr *out)
+{
+    int N = Ki->nrows;
+    if (Ke->nrows != N || Ke->nnz != Ki->nnz) return OC_EINVAL;
+    for (int p = 0; p <= N; p++)
+        if (Ki->rp[p] != Ke->rp[p]) return OC_EINVAL;
+    for (int64_t t = 0; t < Ki->nnz; t++)
+        if (Ki->ci[t] != Ke->ci[t]) return OC_EINVAL;
+    out->nrows = out->ncols = 2 * N;
+    out->nnz = 4 * Ki->nnz;
+    out->rp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * N + 1));
+    out->ci = (int *)malloc(sizeof(int) * (size_t)out->nnz);
+    out->v = (double *)malloc(sizeof(double) * (size_t)out->nnz);
+    if (!out->rp || !out->ci || !out->v) {
+        oc_csr_free(out);
+        return OC_ENOMEM;
+    }
+    int64_t o = 0;
+    for (int p = 0; p < N; p++) {
+        for (int f = 0; f < 2; f++) {            /* row 2p + f */
+            out->rp[2 * p + f] = o;
+            for (int64_t t = Ki->rp[p]; t < Ki->rp[p + 1]; t++) {
+                int q = Ki->ci[t];
+                double kk = Ki->v[t] + Ke->v[t];
+                out->ci[o] = 2 * q;                 /* (f, v) entry */
+                out->v[o] = (f == 0 && q == p) ? 1.0 : 0.0;
+                o++;
+                out->ci[o] = 2 * q + 1;             /* (f, u) entry */
+                out->v[o] = f == 1 ? kk : 0.0;
+                o++;
+            }
+        }
+    }
+    out->rp[2 * N] = o;
+    return 0;
+}
+
+/* y = (c M + Ai) x on the node pattern of Ki */
+static void parabolic_apply(const oc_csr *Ki, const double *M, double c, const double *x, double *y)
+{
+    for (int p = 0; p < Ki->nrows; p++) {
+        double a = 0.0;
+        for (int64_t t = Ki->rp[p]; t < Ki->rp[p + 1]; t++) a = a + Ki->v[t] * x[Ki->ci[t]];
+        y[p] = c * M[p] * x[p] + a;
+    }
+}
+
+int oc_parabolic_cg(const oc_csr *Ki, const double *M, double c, const double *b, double *v,
+                    double rtol, int max_it, int jacobi, int *iters, double *rel_res)
+{
+    int N = Ki->nrows;
+    double *r = (double *)malloc(sizeof(double) * (size_t)N);
+    double *z = (double *)malloc(sizeof(double) * (size_t)N);
+    double *p = (double *)malloc(sizeof(double) * (size_t)N);
+    double *q = (double *)malloc(sizeof(double) * (size_t)N);
+    double *dinv = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!r || !z || !p || !q || !dinv) {
+        free(r); free(z); free(p); free(q); free(dinv);
+        return OC_ENOMEM;
+    }
+    /* Jacobi: inverse of the diagonal of c M + Ai */
+    for (int i = 0; i < N; i++) {
+        double d = c * M[i];
+        for (int64_t t = Ki->rp[i]; t < Ki->rp[i + 1]; t++)
+            if (Ki->ci[t] == i) d = d + Ki->v[t];
+        dinv[i] = jacobi ? 1.0 / d : 1.0;
+    }
+    double nb = sqrt(dot(N, b, b));
+    parabolic_apply(Ki, M, c, v, q);
+    for (int i = 0; i < N; i++) r[i] = b[i] - q[i];
+    double rr = sqrt(dot(N, r, r));
+    int it = 0, ret = 0;
+    if (nb == 0.0) {
+        for (int i = 0; i < N; i++) v[i] = 0.0;
+        rr = 0.0;
+    } else if (rr > rtol * nb) {
+        for (int i = 0; i < N; i++) z[i] = dinv[i] * r[i];
+        memcpy(p, z, sizeof(double) * (size_t)N);
+        double rz = dot(N, r, z);
+        ret = OC_ENOTCONV;
+        while (it < max_it) {
+            parabolic_apply(Ki, M, c, p, q);
+            double pq = dot(N, p, q);
+            if (!(pq > 0.0)) {
+                ret = OC_EBREAK;
+                break;
+            }
+            double alpha = rz / pq;
+            for (int i = 0; i < N; i++) {
+                v[i] = v[i] + alpha * p[i];
+                r[i] = r[i] - alpha * q[i];
+            }
+            it++;
+            rr = sqrt(dot(N, r, r));
+            if (rr <= rtol * nb) {
+                ret = 0;
+                break;
+            }
+            for (int i = 0; i < N; i++) z[i] = dinv[i] * r[i];
+            double rz1 = dot(N, r, z);
+            double beta = rz1 / rz;
+            for (int i = 0; i < N; i++) p[i] = z[i] + beta * p[i];
+            rz = rz1;
+        }
+    }
+    if (iters) *iters = it;
+    if (rel_res) *rel_res = nb > 0.0 ? rr / nb : 0.0;
+    free(r); free(z); free(p); free(q); free(dinv);
+    return ret;
+}
+
+int oc_bd_step_decoupled(const oc_hier *he, const oc_csr *Ki, const double *M, int N, double chi,
+                         double cm, double dt, const oc_rm_params *rm, const double *Iapp,
+                         double *v, double *ue, double *w, double rtol, int max_it, int jacobi,
+                         int *it_ell, int *it_par)
+{
+    int n = 2 * N;
+    if (N < 1 || Ki->nrows != N || he->A[0].nrows != n) return OC_EINVAL;
+    double *f = (double *)malloc(sizeof(double) * (size_t)n);
+    double *x = (double *)malloc(sizeof(double) * (size_t)n);
+    double *kv = (double *)malloc(sizeof(double) * (size_t)N);
+    double *b = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!f || !x || !kv || !b) {
+        free(f); free(x); free(kv); free(b);
+        return OC_ENOMEM;
+    }
+    double c = (chi * cm) / dt;
+    /* Eq. 6: (Ai + Ae) u_e^n = -Ai v^n, in the block form (0, u_e) */
+    oc_spmv(Ki, v, kv);
+    for (int k = 0; k < N; k++) {
+        f[2 * k] = 0.0;
+        f[2 * k + 1] = -kv[k];
+        x[2 * k] = 0.0;
+        x[2 * k + 1] = ue[k];
+    }
+    int ie = 0, ip = 0;
+    double rr, tr;
+    int rc = oc_pcg(he, f, x, 1, rtol, max_it, &ie, &rr, &tr);
+    for (int k = 0; k < N; k++) ue[k] = x[2 * k + 1];
+    if (rc == 0) {
+        /* Eq. 4 and Eq. 7 */
+        oc_spmv(Ki, ue, kv);
+        for (int k = 0; k < N; k++) {
+            double vk = v[k];
+            double wn = (w[k] + dt * rm->eta2 * vk / rm->vp) / (1.0 + dt * rm->eta2 * rm->eta3);
+            double iion = rm->G * vk * (1.0 - vk / rm->vth) * (1.0 - vk / rm->vp) + rm->eta1 * vk * wn;
+            b[k] = c * M[k] * vk - kv[k] + M[k] * (Iapp[k] - chi * iion);
+            w[k] = wn;
+        }
+        rc = oc_parabolic_cg(Ki, M, c, b, v, rtol, max_it, jacobi, &ip, &rr);
+    }
+    if (it_ell) *it_ell = ie;
+    if (it_par) *it_par = ip;
+    free(f); free(x); free(kv); free(b);
+    return rc;
+}

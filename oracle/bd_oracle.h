@@ -130,6 +130,29 @@ int oc_bd_step(const oc_hier *h, const double *M, int N, double chi, double cm,
                double *v, double *ue, double *w, double rtol, int max_it,
                int *iters);
 
+/* ---- f4: the paper's decoupled scheme (Section 2.2, Eqs. 4-7 as printed) --
+ * Elliptic operator Ai + Ae (symmetric positive semi-definite, null vector 1)
+ * in the 2x2-block form the hierarchy code takes: block (p,q) =
+ * [delta_pq, 0; 0, Ki_pq + Ke_pq] on the pattern of Ki (explicit zeros kept),
+ * so the u-field of the block hierarchy is smoothed aggregation on Ai + Ae and
+ * the v-field an identity that stays zero when its right-hand side is. */
+int oc_elliptic_block(const oc_csr *Ki, const oc_csr *Ke, oc_csr *out);
+
+/* Parabolic system (c M + Ai) v = b (Eq. 7, symmetric positive definite) by
+ * CG, Jacobi-preconditioned when jacobi != 0, unpreconditioned otherwise (the
+ * paper's GPU runs), from v (warm start), to ||r||_2 <= rtol ||b||_2. */
+int oc_parabolic_cg(const oc_csr *Ki, const double *M, double c, const double *b, double *v,
+                    double rtol, int max_it, int jacobi, int *iters, double *rel_res);
+
+/* One decoupled step: w^{n+1} (Eq. 4); elliptic (Ai+Ae) u_e^n = -Ai v^n
+ * (Eq. 6) by oc_pcg on the hierarchy he of oc_elliptic_block, warm from ue;
+ * parabolic (c M + Ai) v^{n+1} = c M v^n - Ai u_e^n + M (I_app - chi I_ion)
+ * (Eq. 7, ionic sign as in oc_bd_step) warm from v^n. */
+int oc_bd_step_decoupled(const oc_hier *he, const oc_csr *Ki, const double *M, int N, double chi,
+                         double cm, double dt, const oc_rm_params *rm, const double *Iapp,
+                         double *v, double *ue, double *w, double rtol, int max_it, int jacobi,
+                         int *it_ell, int *it_par);
+
 #ifdef __cplusplus
 }
 #endif
