@@ -57,9 +57,10 @@ def parse_args(argv=None):
     ap.add_argument("--coarse-eq-limit", type=int, default=None)
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
                     help="fp32: FP32 V-cycle inside the FP64 flexible CG")
-    ap.add_argument("--mode", choices=["step", "serve", "batch"], default="step",
+    ap.add_argument("--mode", choices=["step", "serve", "batch", "sweep"], default="step",
                     help="serve: closed-loop capacity and Poisson-load latency of the continuous-batching "
-                         "server; batch: 64 uneven slabs solved in one graph launch vs one solve at a time")
+                         "server; batch: 64 uneven slabs solved in one graph launch vs one solve at a time; "
+                         "sweep: strength threshold 0..0.08, coupled and decoupled schemes")
     ap.add_argument("--requests", type=int, default=16)
     return ap.parse_args(argv)
 
@@ -658,12 +659,85 @@ def run_batch(args):
             "clocks": clk}
 
 
+def run_sweep(args):
+    """Strength threshold sweep (the analogue of the paper's threshold
+    calibration, Section 6.1): for each theta, the coupled scheme (block AMG-PCG
+    per step) and the paper's decoupled scheme (elliptic AMG-PCG + parabolic
+    Jacobi-CG per step), --time-steps steps each from rest with the corner
+    stimulus; hierarchy sizes, setup time, iterations and device solve time."""
+    import torch
+
+    from paper_2311_13914_gb300 import binding as B
+    from paper_2311_13914_gb300 import workloads as W
+
+    rank, local, world = dist_info()
+    torch.cuda.set_device(local)
+    B.lib()
+    mesh, fib, stim, _ = workload(args.workload)
+    p = W.DEFAULT_PARAMS
+    T = args.time_steps
+    stream = torch.cuda.Stream()
+    sysh = B.bd_assemble(mesh, p, torch.tensor(fib.reshape(-1), device="cuda"), stream=stream)
+    stim_d = torch.tensor(stim, device="cuda")
+    rows = []
+
+    def levels(h):
+        info = [B.amg_level_info(h, l) for l in range(B.amg_num_levels(h))]
+        return [i["n"] for i in info], sum(i["nnz"] for i in info) / info[0]["nnz"]
+
+    for theta in (0.0, 0.02, 0.04, 0.06, 0.08):
+        base = vars(args).copy()
+        base["theta"] = theta
+        opts = amg_opts(B, argparse.Namespace(**base))
+        row = {"theta": theta}
+        for scheme in ("coupled", "decoupled"):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            h = (B.amg_setup if scheme == "coupled" else B.bd_elliptic_setup)(sysh, opts, stream=stream)
+            ev[1].record(stream)
+            stream.synchronize()
+            lv, oc = levels(h)
+            r = {"setup_ms": ev[0].elapsed_time(ev[1]), "levels": lv, "operator_complexity": oc}
+            if scheme == "coupled":
+                sim = B.bd_sim_create(sysh, h, stim=stim_d, stim_ms=STIM_MS, stream=stream)
+                its, ms = 0, 0.0
+                for _ in range(T):
+                    info = B.bd_step(sim, 1, stream=stream)
+                    its += info["iters"]
+                    ms += info["solve_ms"]
+                r.update(iters_per_step=its / T, solve_ms_per_step=ms / T)
+            else:
+                sim = B.bd_dsim_create(sysh, h, stim=stim_d, stim_ms=STIM_MS, jacobi=True, stream=stream)
+                ie_s, ip_s, me, mp = 0, 0, 0.0, 0.0
+                for _ in range(T):
+                    ie, ip = B.bd_dsim_step(sim, 1, stream=stream)
+                    ie_s += ie["iters"]
+                    ip_s += ip["iters"]
+                    me += ie["solve_ms"]
+                    mp += ip["solve_ms"]
+                r.update(elliptic_iters_per_step=ie_s / T, elliptic_ms_per_step=me / T,
+                         parabolic_iters_per_step=ip_s / T, parabolic_ms_per_step=mp / T)
+            sim.close()
+            h.close()
+            row[scheme] = r
+        rows.append(row)
+    ref = next(r for r in rows if r["theta"] == 0.06)
+    return {"metric": "strength-threshold sweep: AMG-PCG iterations and device time per time step",
+            "value": 1e3 / ref["coupled"]["solve_ms_per_step"], "unit": "solves/s (coupled, theta 0.06)",
+            "n_gpus": 1, "higher_is_better": True, "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{mesh['nx']}x{mesh['ny']}x{mesh['nz']} slab, {T} time steps from rest, "
+                                   f"corner stimulus; decoupled parabolic solve Jacobi-CG",
+                       "sweep": rows}}
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.mode == "serve":
         out = run_serve(args)
     elif args.mode == "batch":
         out = run_batch(args)
+    elif args.mode == "sweep":
+        out = run_sweep(args)
     else:
         out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:

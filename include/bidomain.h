@@ -294,6 +294,39 @@ int bd_sim_get_state(const bd_sim *s, double *v, double *ue, double *w, int on_d
 int bd_step(bd_sim *s, int nsteps, const solve_options *opts, void *stream, solve_info *last);
 void bd_sim_destroy(bd_sim *s);
 
+/* ---- the paper's decoupled scheme (Section 2.2, Eqs. 4-7 as printed) ------
+ * Per step: the gating update (Eq. 4); the elliptic system
+ * (Ai + Ae) u_e^n = -Ai v^n (Eq. 6) by projected AMG-PCG, warm from the
+ * previous u_e; the parabolic system (c M + Ai) v^{n+1} = c M v^n - Ai u_e^n
+ * + M (I_app - chi I_ion(v^n, w^{n+1})) (Eq. 7, ionic sign as in bd_step) by
+ * CG from v^n, Jacobi-preconditioned (jacobi = 1) or unpreconditioned (0, the
+ * paper's GPU runs).  Both solves stop at ||r||_2 <= rtol ||f||_2.
+ *
+ * bd_elliptic_setup builds the hierarchy of the elliptic operator in the
+ * block form the hierarchy code takes, [I, 0; 0, Ai + Ae] on the node pattern
+ * (its u-field is smoothed aggregation on Ai + Ae with the strength of
+ * amg_options; the identity v-field stays zero), with the same options and
+ * determinism as amg_setup.  A decoupled simulation borrows sys and that
+ * hierarchy (which must outlive it) and owns v, u_e, w (N each, zero at
+ * creation).  bd_dsim_step runs nsteps steps; `elliptic` and `parabolic`
+ * (either may be NULL) receive the last step's solves and the total
+ * iteration counts; solve_ms of `parabolic` is its device time.  Returns the
+ * first failing solve's status (BD_EINVAL for a hierarchy that was not built
+ * by bd_elliptic_setup). */
+typedef struct bd_dsim bd_dsim;
+int bd_elliptic_setup(const bd_system *sys, const amg_options *opts, void *stream,
+                      amg_hierarchy **out);
+int bd_dsim_create(const bd_system *sys, amg_hierarchy *h_elliptic, const bd_rm_params *rm,
+                   const double *stim, int stim_on_device, double stim_ms, int jacobi,
+                   void *stream, bd_dsim **out);
+int bd_dsim_set_state(bd_dsim *s, const double *v, const double *ue, const double *w,
+                      int on_device, void *stream);
+int bd_dsim_get_state(const bd_dsim *s, double *v, double *ue, double *w, int on_device,
+                      void *stream);
+int bd_dsim_step(bd_dsim *s, int nsteps, const solve_options *opts, void *stream,
+                 solve_info *elliptic, solve_info *parabolic);
+void bd_dsim_destroy(bd_dsim *s);
+
 /* ---- serving: continuous batching of simulations ---------------------------
  * A request is a whole simulation (slab, fibre table, stimulus, number of time
  * steps, as for bd_assemble / bd_sim_create; host arrays, copied at submit).

@@ -28,6 +28,7 @@ UNITS = {
     "amg_solve.cu": [],
     "bd_step.cu": [],
     "bd_serve.cu": [],
+    "bd_decoupled.cu": [],
 }
 
 

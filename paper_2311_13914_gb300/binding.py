@@ -102,6 +102,8 @@ EXPORTS = (
     "amg_vcycle", "amg_solve", "amg_destroy", "amg_batch_create", "amg_batch_solve",
     "amg_batch_destroy", "amg_profile_enable", "amg_profile_read",
     "bd_sim_create", "bd_sim_set_state", "bd_sim_get_state", "bd_step", "bd_sim_destroy",
+    "bd_elliptic_setup", "bd_dsim_create", "bd_dsim_set_state", "bd_dsim_get_state", "bd_dsim_step",
+    "bd_dsim_destroy",
     "bd_server_options_default", "bd_server_create", "bd_server_submit", "bd_server_tick",
     "bd_server_drain", "bd_server_request", "bd_server_result", "bd_server_stats",
     "bd_server_destroy",
@@ -164,6 +166,15 @@ def lib():
             L.bd_step.argtypes = [_vp, C.c_int, _P(SolveOptions), _vp, _P(SolveInfo)]
             L.bd_sim_destroy.argtypes = [_vp]
             L.bd_sim_destroy.restype = None
+            L.bd_elliptic_setup.argtypes = [_vp, _P(AmgOptions), _vp, _P(_vp)]
+            L.bd_dsim_create.argtypes = [_vp, _vp, _P(RmParams), _vp, C.c_int, C.c_double, C.c_int,
+                                         _vp, _P(_vp)]
+            L.bd_dsim_set_state.argtypes = [_vp, _vp, _vp, _vp, C.c_int, _vp]
+            L.bd_dsim_get_state.argtypes = [_vp, _vp, _vp, _vp, C.c_int, _vp]
+            L.bd_dsim_step.argtypes = [_vp, C.c_int, _P(SolveOptions), _vp, _P(SolveInfo),
+                                       _P(SolveInfo)]
+            L.bd_dsim_destroy.argtypes = [_vp]
+            L.bd_dsim_destroy.restype = None
             L.bd_server_options_default.argtypes = [_P(ServerOptions)]
             L.bd_server_options_default.restype = None
             L.bd_server_create.argtypes = [_P(ServerOptions), _P(_vp)]
@@ -503,6 +514,57 @@ def bd_sim_get_state(sim: Sim, N: int, stream=None, out=None):
     _check(lib().bd_sim_get_state(sim.ptr, ptrs[0][0], ptrs[1][0], ptrs[2][0], 0, _stream(stream)),
            "bd_sim_get_state")
     return out
+
+
+# ------------------------------------------------------------------ decoupled scheme
+class DSim(_Handle):
+    _destroy = "bd_dsim_destroy"
+
+
+def bd_elliptic_setup(sys: System, opts: AmgOptions | None = None, stream=None) -> Hierarchy:
+    """Hierarchy of the elliptic operator Ai + Ae (as [I, 0; 0, Ai + Ae])."""
+    out = _vp()
+    o = opts if opts is not None else amg_options_default()
+    _check(lib().bd_elliptic_setup(sys.ptr, C.byref(o), _stream(stream), C.byref(out)),
+           "bd_elliptic_setup")
+    return Hierarchy(out)
+
+
+def bd_dsim_create(sys: System, h_elliptic: Hierarchy, rm: RmParams | None = None, stim=None,
+                   stim_ms: float = 0.0, jacobi: bool = True, stream=None) -> DSim:
+    sp_, dev, ks = _arr(stim, np.float64)
+    out = _vp()
+    r = rm if rm is not None else bd_rm_params_default()
+    _check(lib().bd_dsim_create(sys.ptr, h_elliptic.ptr, C.byref(r), sp_, dev, stim_ms,
+                                int(bool(jacobi)), _stream(stream), C.byref(out)), "bd_dsim_create")
+    return DSim(out, keep=(sys, h_elliptic))
+
+
+def bd_dsim_set_state(sim: DSim, v=None, ue=None, w=None, stream=None):
+    a, d1, k1 = _arr(v, np.float64)
+    b, d2, k2 = _arr(ue, np.float64)
+    c, d3, k3 = _arr(w, np.float64)
+    dev = max(d1, d2, d3)
+    _check(lib().bd_dsim_set_state(sim.ptr, a, b, c, dev, _stream(stream)), "bd_dsim_set_state")
+
+
+def bd_dsim_get_state(sim: DSim, N: int, stream=None):
+    out = (np.zeros(N), np.zeros(N), np.zeros(N))
+    ptrs = [_arr(a, np.float64) for a in out]
+    _check(lib().bd_dsim_get_state(sim.ptr, ptrs[0][0], ptrs[1][0], ptrs[2][0], 0, _stream(stream)),
+           "bd_dsim_get_state")
+    return out
+
+
+def bd_dsim_step(sim: DSim, nsteps: int, opts: SolveOptions | None = None, stream=None,
+                 raise_on_error: bool = True) -> tuple:
+    """Returns (elliptic info, parabolic info) of the last step, with totals."""
+    o = opts if opts is not None else solve_options_default()
+    ie, ip = SolveInfo(), SolveInfo()
+    st = lib().bd_dsim_step(sim.ptr, nsteps, C.byref(o), _stream(stream), C.byref(ie), C.byref(ip))
+    if raise_on_error and st != BD_OK:
+        raise BidomainError(st, "bd_dsim_step")
+    return ie.as_dict(), ip.as_dict()
 
 
 def bd_step(sim: Sim, nsteps: int, opts: SolveOptions | None = None, stream=None,

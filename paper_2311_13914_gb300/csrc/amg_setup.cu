@@ -1264,6 +1264,65 @@ extern "C" int amg_setup(const bd_system *sys, const amg_options *opts, void *st
     return BD_OK;
 }
 
+// The elliptic operator Ai + Ae of the decoupled scheme (Section 2.2, Eq. 6)
+// as the block operator [I, 0; 0, Ai + Ae] on the assembled node pattern, so
+// that the block hierarchy's u-field is smoothed aggregation on Ai + Ae.
+__global__ void k_elliptic_values(int N, const int *__restrict__ rp, const int *__restrict__ ci,
+                                  const double *__restrict__ Ki, const double *__restrict__ Ke,
+                                  double *__restrict__ v)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x)
+        for (int t = rp[p]; t < rp[p + 1]; t++) {
+            v[4 * (size_t)t] = ci[t] == p ? 1.0 : 0.0;
+            v[4 * (size_t)t + 1] = 0.0;
+            v[4 * (size_t)t + 2] = 0.0;
+            v[4 * (size_t)t + 3] = Ki[t] + Ke[t];
+        }
+}
+
+extern "C" int bd_elliptic_setup(const bd_system *sys, const amg_options *opts, void *stream,
+                                 amg_hierarchy **out)
+{
+    if (!sys || !out) return BD_EINVAL;
+    *out = nullptr;
+    amg_options o;
+    amg_options_default(&o);
+    if (opts) o = *opts;
+    BD_TRY(check_opts(&o));
+    cudaStream_t s = (cudaStream_t)stream;
+    amg_hierarchy *h = new (std::nothrow) amg_hierarchy();
+    if (!h) return BD_ENOMEM;
+    h->opts = o;
+    h->prec32 = o.precision == 1;
+    Level &L0 = h->lev[0];
+    L0.N = sys->N;
+    L0.A.nbr = L0.A.nbc = sys->N;
+    L0.A.nb = sys->A.nb;
+    int st;
+    if ((st = L0.A.rp.alloc((size_t)sys->N + 1)) || (st = L0.A.ci.alloc((size_t)sys->A.nb)) ||
+        (st = L0.A.v.alloc(4 * (size_t)sys->A.nb))) {
+        delete h;
+        return st;
+    }
+    if (cudaMemcpyAsync(L0.A.rp.p, sys->A.rp.p, L0.A.rp.bytes(), cudaMemcpyDeviceToDevice, s) ||
+        cudaMemcpyAsync(L0.A.ci.p, sys->A.ci.p, L0.A.ci.bytes(), cudaMemcpyDeviceToDevice, s)) {
+        delete h;
+        return BD_ECUDA;
+    }
+    k_elliptic_values<<<grid_for(sys->N, 256), 256, 0, s>>>(sys->N, sys->A.rp.p, sys->A.ci.p, sys->Ki.p,
+                                                            sys->Ke.p, L0.A.v.p); ::bd::note_launch();
+    if (cudaGetLastError() != cudaSuccess) {
+        delete h;
+        return BD_ECUDA;
+    }
+    if ((st = setup_from_level0(h, s)) || (st = prepare_solve(h, s))) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return BD_OK;
+}
+
 extern "C" int amg_setup_from_csr(int n, const int *row_ptr, const int *col, const double *val,
                                   int on_device, const amg_options *opts, void *stream,
                                   amg_hierarchy **out)
