@@ -83,7 +83,10 @@ typedef struct {
                               an FP64 flexible CG (Polak-Ribiere beta) (0)          */
     int autotune;          /* 0: lanes per block row of the V-cycle's block-CSR
                               operators from a row-length rule; 1: amg_setup times
-                              every candidate on this GPU and keeps the fastest.
+                              the candidates of every operator of at least 20000
+                              blocks on this GPU (cold L2, median of three) and
+                              keeps the fastest; it needs a 192 MB scratch buffer
+                              for a moment and keeps the rule without one.
                               Either way the choice is fixed per hierarchy, so its
                               solves are reproducible; the two choices differ in
                               the summation order of row sums (last bits) (0)       */

@@ -369,6 +369,8 @@ static int pow2_at_least(long long v)
     return p;
 }
 
+constexpr long long kHashProducts = 4096;  // products per row up to which the hash path is used
+
 template <int BS>
 static int spgemm(int nrows, int ncols, const int *arp, const int *aci, const double *av,
                   const int *brp, const int *bci, const double *bv, DBuf<int> &crp, DBuf<int> &cci,
@@ -391,6 +393,21 @@ static int spgemm(int nrows, int ncols, const int *arp, const int *aci, const do
     DBuf<int> flag;
     BD_TRY(flag.alloc(1));
     BD_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+    // Rows with few products (the fine levels' many short rows) go to the
+    // warp-per-row hash path: the dense path's thread block per row then idles
+    // most of its threads and synchronises once per middle index.  Both paths
+    // accumulate every entry in the same order, so the choice changes no bit.
+    std::vector<int> ub;
+    long long mub = 1;
+    if (nrows > 0) {
+        k_spgemm_bound<<<(nrows + 255) / 256, 256, 0, s>>>(nrows, arp, aci, brp, cnt.p); ::bd::note_launch();
+        BD_LAUNCH_CHECK();
+        ub.resize((size_t)nrows);
+        BD_CUDA(cudaMemcpyAsync(ub.data(), cnt.p, ub.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+        BD_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < nrows; i++) mub = std::max<long long>(mub, ub[i]);
+        if (mub <= kHashProducts) dense = false;
+    }
     int HCn = 0, warps_n = 1;
     if (dense) {
         BD_TRY(mark.alloc((size_t)grid * ncols));
@@ -399,13 +416,6 @@ static int spgemm(int nrows, int ncols, const int *arp, const int *aci, const do
         k_spgemm_count<BS><<<grid, 128, 0, s>>>(nrows, arp, aci, brp, bci, ncols, mark.p, cnt.p); ::bd::note_launch();
         BD_LAUNCH_CHECK();
     } else {
-        k_spgemm_bound<<<(nrows + 255) / 256, 256, 0, s>>>(nrows, arp, aci, brp, cnt.p); ::bd::note_launch();
-        BD_LAUNCH_CHECK();
-        std::vector<int> ub((size_t)nrows);
-        BD_CUDA(cudaMemcpyAsync(ub.data(), cnt.p, ub.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
-        BD_CUDA(cudaStreamSynchronize(s));
-        long long mub = 1;
-        for (int i = 0; i < nrows; i++) mub = std::max<long long>(mub, ub[i]);
         int HCs = pow2_at_least(2 * std::min<long long>(mub, kMaxSortSeg));
         if (HCs < 32) HCs = 32;
         int warps = std::max(1, std::min(8, (int)((192 << 10) / ((size_t)HCs * 4))));

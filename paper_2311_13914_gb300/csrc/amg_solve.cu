@@ -1076,23 +1076,55 @@ static void xr_update(const amg_hierarchy *h, int N, double2 *x, double2 *r, con
 }
 
 // ------------------------------------------------------------------ lane autotuning
-// Mean time of three launches of one block-CSR operator with T lanes per row
-// (after one untimed launch), with the residual epilogue out = f - M x.
+// Candidates: powers of two from (average blocks per row)/16 lanes per row
+// to 4x the average, 64/128/256 meaning a thread block per row (rows of 32
+// blocks and more only).  Each is timed three times, every launch after L2 has been
+// flushed by writing a buffer larger than it (in the V-cycle every coarse
+// operator runs after the finest level has streamed far more than L2
+// through, so cold timings rank the candidates the way the solve sees them);
+// the median counts.  All launches of one operator are queued with their
+// events and read after a single synchronisation.
+constexpr int kLaneCands = 9, kLaneReps = 3;
+constexpr long long kTuneMinBlocks = 20000;  // smaller operators keep the row-length rule
+
 template <class S>
-static int time_bsr(const BSR &M, const S *vals, int T, const v2<S> *x, const v2<S> *f, v2<S> *out,
-                    cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, float *ms)
+static int tune_operator(const BSR &M, const S *vals, const v2<S> *x, const v2<S> *f, v2<S> *out,
+                         void *flush, size_t flush_bytes, cudaEvent_t (*ev)[kLaneReps][2], cudaStream_t s,
+                         int *lanes)
 {
+    const double avg = M.nbr > 0 ? (double)M.nb / M.nbr : 1.0;
     const EpiResid<S> epi{f, out};
-    BD_TRY(launch_bsr<S>(M, vals, T, GatherVec<S>{x}, epi, s));
-    BD_CUDA(cudaEventRecord(e0, s));
-    for (int k = 0; k < 3; k++) BD_TRY(launch_bsr<S>(M, vals, T, GatherVec<S>{x}, epi, s));
-    BD_CUDA(cudaEventRecord(e1, s));
-    BD_CUDA(cudaEventSynchronize(e1));
-    BD_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    // rows of avg blocks: from avg/16 lanes (16 blocks per lane) up to 4 avg,
+    // a thread block per row only for rows of 32 blocks and more
+    int Tlo = 1, Thi = 256;
+    while (Tlo * 16 < avg && Tlo < 32) Tlo <<= 1;
+    while (Thi > 1 && Thi > 4.0 * avg) Thi >>= 1;
+    if (avg < 32.0) Thi = std::min(Thi, 32);
+    Thi = std::max(Thi, Tlo);
+    int cand[kLaneCands], nc = 0;
+    for (int T = Tlo; T <= Thi && nc < kLaneCands; T <<= 1) cand[nc++] = T;
+    for (int c = 0; c < nc; c++)
+        for (int k = 0; k < kLaneReps; k++) {
+            BD_CUDA(cudaMemsetAsync(flush, k, flush_bytes, s));
+            BD_CUDA(cudaEventRecord(ev[c][k][0], s));
+            BD_TRY(launch_bsr<S>(M, vals, cand[c], GatherVec<S>{x}, epi, s));
+            BD_CUDA(cudaEventRecord(ev[c][k][1], s));
+        }
+    BD_CUDA(cudaStreamSynchronize(s));
+    float best = 0.0f;
+    for (int c = 0; c < nc; c++) {
+        float t[kLaneReps];
+        for (int k = 0; k < kLaneReps; k++) BD_CUDA(cudaEventElapsedTime(&t[k], ev[c][k][0], ev[c][k][1]));
+        const float med = std::max(std::min(t[0], t[1]), std::min(std::max(t[0], t[1]), t[2]));
+        if (c == 0 || med < best) {
+            best = med;
+            *lanes = cand[c];
+        }
+    }
     return BD_OK;
 }
 
-// Time every candidate lane count of every block-CSR operator the V-cycle
+// Time the candidate lane counts of every block-CSR operator the V-cycle
 // applies (A where the finest level is not sliced ELL, R and P) on this GPU
 // and keep the fastest.  The workspace vectors serve as operands; their
 // contents do not matter.  Lanes change the order of a row's sum, so the
@@ -1100,39 +1132,36 @@ static int time_bsr(const BSR &M, const S *vals, int T, const v2<S> *x, const v2
 template <class S>
 static int autotune_lanes(amg_hierarchy *h, cudaStream_t s)
 {
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-        if (e0) cudaEventDestroy(e0);
-        return BD_ECUDA;
+    const size_t flush_bytes = (size_t)192 << 20;  // > the 126 MB L2
+    DBuf<unsigned char> flush;
+    if (flush.alloc(flush_bytes) != BD_OK) {  // no room to time: the row-length rule stays
+        cudaGetLastError();
+        return BD_OK;
     }
+    cudaEvent_t ev[kLaneCands][kLaneReps][2] = {};
     int st = BD_OK;
+    for (auto &c : ev)
+        for (auto &r : c)
+            for (cudaEvent_t &e : r)
+                if (st == BD_OK && cudaEventCreate(&e) != cudaSuccess) st = BD_ECUDA;
     for (int l = 0; l < h->nlev - 1 && st == BD_OK; l++) {
         Level &L = h->lev[l];
         const LV<S> lv = view<S>(h, l), cv = view<S>(h, l + 1);
         for (int op = 0; op < 3 && st == BD_OK; op++) {
             if (op == 0 && l == 0 && h->sell.valid) continue;
             const BSR &M = op == 0 ? L.A : (op == 1 ? L.R : L.P);
+            if (M.nb < kTuneMinBlocks) continue;
             const S *vals = op == 0 ? lv.Av : (op == 1 ? lv.Rv : lv.Pv);
             const v2<S> *x = op == 0 ? lv.u : (op == 1 ? lv.r : cv.u);
             const v2<S> *f = op == 1 ? cv.f : lv.f;
             v2<S> *out = op == 0 ? lv.r : (op == 1 ? cv.r : lv.w);
-            const double avg = M.nbr > 0 ? (double)M.nb / M.nbr : 1.0;
-            float best = 0.0f;
-            int bestT = L.lanes[op];
-            for (int T = 1; T <= 256 && st == BD_OK; T <<= 1) {
-                if (T >= 64 && avg < 32.0) break;  // a thread block per short row never wins
-                float ms = 0.0f;
-                st = time_bsr<S>(M, vals, T, x, f, out, s, e0, e1, &ms);
-                if (st == BD_OK && (T == 1 || ms < best)) {
-                    best = ms;
-                    bestT = T;
-                }
-            }
-            L.lanes[op] = bestT;
+            st = tune_operator<S>(M, vals, x, f, out, flush.p, flush_bytes, ev, s, &L.lanes[op]);
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    for (auto &c : ev)
+        for (auto &r : c)
+            for (cudaEvent_t e : r)
+                if (e) cudaEventDestroy(e);
     return st;
 }
 
