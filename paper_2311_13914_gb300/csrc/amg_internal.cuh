@@ -39,7 +39,9 @@ struct FineSell {
     int nslices = 0;
     long long slots = 0;        // padded slots (x 32 lanes)
     DBuf<int> sptr;             // nslices + 1, slot offset of each slice
-    DBuf<int> col;              // slots * 32
+    DBuf<int> col;              // slots * 32 column (FP64 kernels: an index costs no FP64 time)
+    DBuf<unsigned char> code;   // slots * 32: neighbour q = p + off[code] (27-point stencil; FP32)
+    int off[27] = {};           // node-index offset of each stencil position
     DBuf<double> kk;            // slots * 32 * 2: (Ki, Ke)
     DBuf<double> cm;            // c M_p per node
     DBuf<float> kk32, cm32;     // FP32 copies for the FP32 V-cycle

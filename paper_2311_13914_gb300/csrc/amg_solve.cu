@@ -138,18 +138,39 @@ __device__ __forceinline__ int share_hi(int n)
     return min(n, (int)((((long long)n + 31) >> 5) * (blockIdx.x + 1) / gridDim.x) * 32);
 }
 
+// Neighbour offsets of the 27-point stencil of a structured slab, passed by
+// value and staged in shared memory (a warp's lanes index it divergently).
+struct Stencil {
+    int off[27];
+};
+__device__ __forceinline__ void stage_stencil(const Stencil &st, int *off)
+{
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < 27; i++) off[i] = st.off[i];  // constant indices: no local copy
+    }
+    __syncthreads();
+}
+
 // One thread per row; slot j of slice s holds entry j of its 32 rows
-// contiguously, so every slot is one coalesced (Ki, Ke) load and one 128-byte
-// column load per warp.  Per node pair: s = v_q + u_q, a += Ki s, b += Ke u_q;
+// contiguously, so every slot is one coalesced (Ki, Ke) load and one column
+// load per warp.  FP32 (HBM-bound) reads 1-byte stencil codes (the
+// neighbour's position in the 27-point stencil) instead of 4-byte columns:
+// 9 instead of 12 bytes per node pair; FP64 (bound by its FP64 pipe as much
+// as by HBM) keeps the columns, which spare it the shared-memory lookup.  Per node pair: s = v_q + u_q, a += Ki s, b += Ke u_q;
 // then y_v = c M_p v_p + a, y_u = a + b.  SU: the gathered vector is stored as
 // (v + u, u), which saves the add per node pair (two FP64 operations instead
 // of three where the FP64 pipe is the limit).
 template <class S, class G, class E, bool SU = false, int MINB = 8>
 __global__ void __launch_bounds__(256, MINB) k_sell(int N, const int *__restrict__ sptr,
                                                const int *__restrict__ col,
+                                               const unsigned char *__restrict__ code, Stencil st,
                                                const v2<S> *__restrict__ kk,
                                                const S *__restrict__ cm, G gather, E epi)
 {
+    constexpr bool CODED = sizeof(S) == 4;
+    __shared__ int off[27];
+    if (CODED) stage_stencil(st, off);
     const int lane = threadIdx.x & 31, e = share_hi(N);
     for (int p = share_lo(N) + threadIdx.x; p < e; p += blockDim.x) {
         const int sl = p >> 5;
@@ -158,7 +179,7 @@ __global__ void __launch_bounds__(256, MINB) k_sell(int N, const int *__restrict
 #pragma unroll (MINB >= 8 ? 4 : 8)
         for (int j = sptr[sl]; j < j1; j++) {
             const size_t idx = (size_t)j * 32 + lane;
-            const int q = col[idx];
+            const int q = CODED ? p + off[code[idx]] : col[idx];
             const v2<S> k = kk[idx];
             const v2<S> x = gather(q);
             a = fma(k.x, SU ? x.x : x.x + x.y, a);
@@ -370,22 +391,37 @@ __global__ void k_sell_width(int N, const int *__restrict__ rp, int *__restrict_
     w[sl] = mx;
 }
 
-__global__ void k_sell_fill(int N, const int *__restrict__ rp, const int *__restrict__ ci,
+// Node k = i + X (j + Y l) (X = nx+1, Y = ny+1); the neighbour q of p sits
+// at stencil position 9 (lq - lp + 1) + 3 (jq - jp + 1) + (iq - ip + 1).
+__global__ void k_sell_fill(int N, int X, int Y, const int *__restrict__ rp, const int *__restrict__ ci,
                             const double *__restrict__ Ki, const double *__restrict__ Ke,
                             const double *__restrict__ M, double c, const int *__restrict__ sptr,
-                            int *__restrict__ col, double2 *__restrict__ kk, double *__restrict__ cm)
+                            int *__restrict__ col, unsigned char *__restrict__ code, double2 *__restrict__ kk,
+                            double *__restrict__ cm, int *__restrict__ bad)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
     int sl = p >> 5, lane = p & 31;
     int j0 = sptr[sl], width = sptr[sl + 1] - j0, b = rp[p], len = rp[p + 1] - b;
+    const int ip = p % X, jp = (p / X) % Y, lp = p / (X * Y);
     for (int j = 0; j < width; j++) {
         size_t idx = (size_t)(j0 + j) * 32 + lane;
         if (j < len) {
-            col[idx] = ci[b + j];
+            const int q = ci[b + j];
+            const int di = q % X - ip, dj = (q / X) % Y - jp, dl = q / (X * Y) - lp;
+            if (di < -1 || di > 1 || dj < -1 || dj > 1 || dl < -1 || dl > 1) {
+                atomicOr(bad, 1);
+                col[idx] = p;
+                code[idx] = 13;
+                kk[idx] = make_double2(0.0, 0.0);
+                continue;
+            }
+            col[idx] = q;
+            code[idx] = (unsigned char)(9 * (dl + 1) + 3 * (dj + 1) + (di + 1));
             kk[idx] = make_double2(Ki[b + j], Ke[b + j]);
         } else {
             col[idx] = p;
+            code[idx] = 13;  // the row itself, with zero weights
             kk[idx] = make_double2(0.0, 0.0);
         }
     }
@@ -406,16 +442,35 @@ int build_fine_sell(amg_hierarchy *h, const bd_system *sys, cudaStream_t s)
     BD_TRY(exclusive_scan(w.p, F.sptr.p, F.nslices, &slots, s));
     F.slots = slots;
     BD_TRY(F.col.alloc((size_t)slots * 32));
+    BD_TRY(F.code.alloc((size_t)slots * 32));
     BD_TRY(F.kk.alloc((size_t)slots * 64));
     BD_TRY(F.cm.alloc((size_t)N));
+    DBuf<int> bad;
+    BD_TRY(bad.alloc(1));
+    BD_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+    const int X = sys->mesh.nx + 1, Y = sys->mesh.ny + 1;
+    for (int dl = 0; dl < 3; dl++)
+        for (int dj = 0; dj < 3; dj++)
+            for (int di = 0; di < 3; di++)
+                F.off[9 * dl + 3 * dj + di] = (dl - 1) * X * Y + (dj - 1) * X + (di - 1);
     const bd_params &P = sys->params;
-    k_sell_fill<<<(N + 255) / 256, 256, 0, s>>>(N, sys->A.rp.p, sys->A.ci.p, sys->Ki.p, sys->Ke.p,
-                                                sys->M.p, (P.chi * P.cm) / P.dt, F.sptr.p, F.col.p,
-                                                (double2 *)F.kk.p, F.cm.p); ::bd::note_launch();
+    k_sell_fill<<<(N + 255) / 256, 256, 0, s>>>(N, X, Y, sys->A.rp.p, sys->A.ci.p, sys->Ki.p, sys->Ke.p,
+                                                sys->M.p, (P.chi * P.cm) / P.dt, F.sptr.p, F.col.p, F.code.p,
+                                                (double2 *)F.kk.p, F.cm.p, bad.p); ::bd::note_launch();
     BD_LAUNCH_CHECK();
+    int hbad = 0;
+    BD_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     BD_CUDA(cudaStreamSynchronize(s));
+    if (hbad) return BD_EINVAL;  // not a 27-point pattern: the assembled system was corrupted
     F.valid = true;
     return BD_OK;
+}
+
+static Stencil stencil_of(const FineSell &F)
+{
+    Stencil st;
+    for (int i = 0; i < 27; i++) st.off[i] = F.off[i];
+    return st;
 }
 
 // operator application of level l in precision S: sliced ELL on the finest
@@ -429,7 +484,7 @@ static int apply_level(amg_hierarchy *h, int l, const LV<S> &lv, G g, E e, cudaS
         const FineSell &F = h->sell;
         constexpr int MB = sizeof(S) == 8 ? 4 : 8;  // FP64: fewer, deeper-pipelined threads
         int grid = (int)std::min<long long>(((long long)L.N + 31) / 32, (long long)kSM * MB);
-        k_sell<S, G, E, SU, MB><<<grid, 256, 0, s>>>(L.N, F.sptr.p, F.col.p, lv.kk, lv.cm, g, e); ::bd::note_launch();
+        k_sell<S, G, E, SU, MB><<<grid, 256, 0, s>>>(L.N, F.sptr.p, F.col.p, F.code.p, stencil_of(F), lv.kk, lv.cm, g, e); ::bd::note_launch();
         BD_LAUNCH_CHECK();
         return BD_OK;
     }
@@ -480,15 +535,15 @@ void prof_collect(amg_hierarchy *h)
 }
 
 // Algorithmic bytes of one finest-level operator application in precision S:
-// the stored matrix once (sliced ELL: Ki, Ke and a column per slot incl.
-// padding, slice offsets, c M; block CSR: four values and a column per block,
-// row offsets) and `vec` per-node vector streams of two S each.
-// Flops: 2 per scalar nonzero (8 per 2x2 block).
+// the stored matrix once (sliced ELL: Ki, Ke and a 4-byte column (FP64) or a
+// 1-byte stencil code (FP32) per slot incl. padding, slice offsets, c M;
+// block CSR: four values and a column per block, row offsets) and `vec`
+// per-node vector streams of two S each.
 template <class S>
 static double fine_bytes(const amg_hierarchy *h, const Level &L, int vec)
 {
     const double sz = (double)sizeof(S);
-    double mat = h->sell.valid ? (2 * sz + 4.0) * 32.0 * (double)h->sell.slots +
+    double mat = h->sell.valid ? (2 * sz + (sz == 4 ? 1.0 : 4.0)) * 32.0 * (double)h->sell.slots +
                                      4.0 * (h->sell.nslices + 1) + sz * L.N
                                : (4 * sz + 4.0) * (double)L.A.nb + 4.0 * (L.N + 1);
     return mat + 2 * sz * vec * (double)L.N;
