@@ -929,6 +929,69 @@ __global__ void k_coarse_factor(int n, double *A, const double *__restrict__ z, 
     }
 }
 
+// Larger coarsest levels: the same rank-one-fixed matrix, inverted in place by
+// Gauss-Jordan elimination without pivoting (the matrix is symmetric positive
+// definite), one launch per pivot over the whole matrix (a thread block per
+// row segment, so the row's multiplier is one division per block).  Step k reads the
+// pivot row and column of the previous step from scratch buffers (double
+// buffered by the parity of k) and writes those of step k + 1, so no entry is
+// read after it is overwritten.
+__global__ void k_coarse_stats(int n, const double *__restrict__ A, const double *__restrict__ z,
+                               double *__restrict__ out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double smax = 0.0, zz = 0.0;
+    for (int i = 0; i < n; i++) {
+        double d = A[(size_t)i * n + i];
+        if (d > smax) smax = d;
+        zz = zz + z[i] * z[i];
+    }
+    out[0] = smax;
+    out[1] = zz;
+}
+
+// grid: x over columns (blockDim.x threads each), y over rows
+__global__ void k_coarse_rank1(int n, double *__restrict__ A, const double *__restrict__ z,
+                               const double *__restrict__ st, double *__restrict__ row0, double *__restrict__ col0)
+{
+    const double smax = st[0], zz = st[1];
+    const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const size_t e = (size_t)i * n + j;
+    const double a = A[e] + (smax * z[i]) * z[j] / zz;
+    A[e] = a;
+    if (i == 0) row0[j] = a;
+    if (j == 0) col0[i] = a;
+}
+
+__global__ void k_gauss_jordan(int n, int k, double *__restrict__ A, const double *__restrict__ row,
+                               const double *__restrict__ col, double *__restrict__ nrow,
+                               double *__restrict__ ncol, int *__restrict__ bad)
+{
+    const double piv = row[k];
+    const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double fi;  // col[i] / piv: one FP64 division per block, not per entry
+    if (threadIdx.x == 0) fi = col[i] / piv;
+    __syncthreads();
+    if (j < n) {
+        const size_t e = (size_t)i * n + j;
+        double a;
+        if (i == k && j == k) {
+            if (!(piv > 0.0)) *bad = 1;
+            a = 1.0 / piv;
+        } else if (i == k) {
+            a = row[j] / piv;
+        } else if (j == k) {
+            a = -fi;
+        } else {
+            a = A[e] - fi * row[j];
+        }
+        A[e] = a;
+        if (i == k + 1) nrow[j] = a;
+        if (j == k + 1) ncol[i] = a;
+    }
+}
+
 __global__ void k_null_vector(int N, const double *__restrict__ B, double *z)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1171,6 +1234,8 @@ static int finish_level_common(Level &L, cudaStream_t s)
     return hbad ? BD_EINVAL : BD_OK;
 }
 
+constexpr int kCoarseSingleBlock = 256;  // coarsest sizes factored by one thread block
+
 static int build_coarsest(amg_hierarchy *h, int l, cudaStream_t s)
 {
     Level &L = h->lev[l];
@@ -1191,8 +1256,27 @@ static int build_coarsest(amg_hierarchy *h, int l, cudaStream_t s)
     BD_TRY(zz.alloc(1));
     BD_TRY(bad.alloc(1));
     BD_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
-    k_coarse_factor<<<1, 256, 0, s>>>(n, Ad.p, h->zc.p, h->cinv.p, zz.p, bad.p); ::bd::note_launch();
-    BD_LAUNCH_CHECK();
+    if (n <= kCoarseSingleBlock) {
+        k_coarse_factor<<<1, 256, 0, s>>>(n, Ad.p, h->zc.p, h->cinv.p, zz.p, bad.p); ::bd::note_launch();
+        BD_LAUNCH_CHECK();
+    } else {
+        DBuf<double> st, rows, cols;
+        BD_TRY(st.alloc(2));
+        BD_TRY(rows.alloc(2 * (size_t)n));
+        BD_TRY(cols.alloc(2 * (size_t)n));
+        k_coarse_stats<<<1, 32, 0, s>>>(n, Ad.p, h->zc.p, st.p); ::bd::note_launch();
+        const dim3 g((n + 127) / 128, n);
+        k_coarse_rank1<<<g, 128, 0, s>>>(n, Ad.p, h->zc.p, st.p, rows.p, cols.p); ::bd::note_launch();
+        for (int k = 0; k < n; k++) {
+            double *r0 = rows.p + (size_t)(k & 1) * n, *c0 = cols.p + (size_t)(k & 1) * n;
+            double *r1 = rows.p + (size_t)((k + 1) & 1) * n, *c1 = cols.p + (size_t)((k + 1) & 1) * n;
+            k_gauss_jordan<<<g, 128, 0, s>>>(n, k, Ad.p, r0, c0, r1, c1, bad.p); ::bd::note_launch();
+        }
+        BD_LAUNCH_CHECK();
+        BD_CUDA(cudaMemcpyAsync(h->cinv.p, Ad.p, Ad.bytes(), cudaMemcpyDeviceToDevice, s));
+        BD_CUDA(cudaMemcpyAsync(zz.p, st.p + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        BD_CUDA(cudaStreamSynchronize(s));  // the scratch buffers are freed on return
+    }
     int hbad = 0;
     BD_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     BD_CUDA(cudaMemcpyAsync(&h->zz, zz.p, sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -591,6 +591,39 @@ __global__ void k_coarse_solve(int n, const double *__restrict__ cinv, const dou
     }
 }
 
+// The same for larger coarsest levels, over the whole GPU: every block forms
+// z.r itself (same order in each, so all agree), then one warp per row.
+template <class S>
+__global__ void __launch_bounds__(256) k_coarse_solve_wide(int n, const double *__restrict__ cinv,
+                                                           const double *__restrict__ z, double zz,
+                                                           const S *__restrict__ r, S *__restrict__ x)
+{
+    __shared__ double red[8];
+    __shared__ double alpha;
+    double part = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) part += z[i] * (double)r[i];
+    for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += red[w];
+        alpha = zz > 0.0 ? v / zz : 0.0;
+    }
+    __syncthreads();
+    const double a = alpha;
+    const int lane = threadIdx.x & 31;
+    const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int i = warp; i < n; i += nw) {
+        const double *row = cinv + (size_t)i * n;
+        double sacc = 0.0;
+        for (int j = lane; j < n; j += 32) sacc += row[j] * ((double)r[j] - a * z[j]);
+        for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+        if (lane == 0) x[i] = (S)sacc;
+    }
+}
+
 template <class S>
 __global__ void k_copy2(int N, const v2<S> *__restrict__ a, v2<S> *__restrict__ b)
 {
@@ -700,7 +733,12 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
         const S *f = (const S *)(nl == 1 ? f0 : cv.f);
         S *u = (S *)(nl == 1 ? u0 : cv.u);
         size_t smem = sizeof(double) * (size_t)h->nc;
-        k_coarse_solve<S><<<1, 1024, smem, s>>>(h->nc, h->cinv.p, h->zc.p, h->zz, f, u); ::bd::note_launch();
+        if (h->nc <= 256) {
+            k_coarse_solve<S><<<1, 1024, smem, s>>>(h->nc, h->cinv.p, h->zc.p, h->zz, f, u); ::bd::note_launch();
+        } else {
+            k_coarse_solve_wide<S><<<(h->nc + 7) / 8, 256, 0, s>>>(h->nc, h->cinv.p, h->zc.p, h->zz, f, u);
+            ::bd::note_launch();
+        }
         BD_LAUNCH_CHECK();
     }
     for (int l = nl - 2; l >= 0; l--)

@@ -280,6 +280,30 @@ def test_autotuned_lanes_solve(B, oracle_lib, precision):
     assert il["iters"] == ig["iters"] and np.array_equal(xl, xg)
 
 
+@pytest.mark.parametrize("m,limit", [(W.SLAB_SMALL, 2000), (W.mesh(32, 32, 10), 4000)])
+def test_large_coarsest_level_matches_oracle(B, oracle_lib, m, limit):
+    """Coarsest levels above 256 unknowns are inverted by multi-block
+    Gauss-Jordan (and above 1024 solved by a multi-block mat-vec): the V-cycle
+    and the PCG solution still meet the oracle's dense Cholesky solve."""
+    fib = W.fibre_table(m)
+    sysh, h = _gpu_hier(B, m, fib, coarse_eq_limit=limit)
+    o = oracle_lib.assemble(m, W.DEFAULT_PARAMS, fib)
+    H = oracle_lib.Hierarchy(o["A"], coarse_eq_limit=limit)
+    nl = B.amg_num_levels(h)
+    sizes = [B.amg_level_info(h, l)["n"] for l in range(nl)]
+    assert sizes == [H.A(l).shape[0] for l in range(H.nlevels)] and sizes[-1] > 256
+    rng = np.random.default_rng(8)
+    r = rng.standard_normal(o["A"].shape[0])
+    r[1::2] -= r[1::2].mean()
+    zo = H.vcycle(r)
+    assert np.linalg.norm(B.amg_vcycle(h, r) - zo) <= 1e-10 * np.linalg.norm(zo)
+    f = W.rhs(o["A"].shape[0], seed=9)
+    xg, ig = B.amg_solve(h, f)
+    xo, io = H.pcg(f, rtol=1e-8)
+    assert ig["status"] == 0 and abs(ig["iters"] - io["iters"]) <= 1
+    assert np.linalg.norm(xg - xo) <= 1e-7 * np.linalg.norm(xo)
+
+
 def test_time_stepping_matches_oracle(B, oracle_lib):
     m = W.mesh(16, 16, 8, 0.6, 0.6, 0.3)
     p = W.DEFAULT_PARAMS
