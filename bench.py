@@ -306,6 +306,24 @@ def run_ours(args):
     elapsed_ms = max_over_ranks(dist, t0.elapsed_time(t1), True)
     value = world * args.steps * T / (elapsed_ms / 1e3)
 
+    # untimed: per-step device time of the solve phase (host-driven loop with
+    # CUDA events around every step), per PCG iteration
+    breakdown = None
+    if rank == 0:
+        sysh = B.bd_assemble(mesh, p, fib_d, stream=stream)
+        h = B.amg_setup(sysh, amg_opts(B, args), stream=stream)
+        sim = B.bd_sim_create(sysh, h, stim=stim_d, stim_ms=STIM_MS, stream=stream)
+        B.amg_profile_enable(h, 2)
+        info = B.bd_step(sim, 2, stream=stream)
+        B.amg_profile_enable(h, 0)
+        its = max(info["total_iters"], 1)
+        bd_ = B.amg_profile_breakdown(h)
+        breakdown = {k: round(1e3 * v[0] / its, 2) for k, v in
+                     sorted(bd_.items(), key=lambda kv: -kv[1][0])}
+        sim.close()
+        h.close()
+        sysh.close()
+
     # end to end through the public API with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -389,6 +407,7 @@ def run_ours(args):
                    "max_true_rel_res": max(rec["true_rel_res"]),
                    "levels": rec.get("levels"), "operator_complexity": rec.get("op_complexity"),
                    "lanes_A_R_P": rec.get("lanes"),
+                   "breakdown_us_per_pcg_iteration": breakdown,
                    "amg_options": {k: getattr(amg_opts(B, args), k) for k in
                                    ("theta", "square_levels", "coarse_eq_limit", "cheb_degree",
                                     "precision", "autotune")}},

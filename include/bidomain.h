@@ -266,7 +266,8 @@ void amg_batch_destroy(amg_batch *b);
  * the finest level needs 2 FMA per stored node pair with its gathered vector
  * in (v + u, u) form, 2 FMA and an add otherwise, where the 2x2-block operator
  * would take 8 flops per block) are summed.  Switching it on resets the sums, switching it off keeps them
- * for amg_profile_read; reading requires no pending work.  While it is on,
+ * for amg_profile_read; reading requires no pending work.  enable: 0 off,
+ * 1 on, 2 on with the per-step breakdown below.  While it is on,
  * solves run the host-driven loop (one launch at a time) instead of the
  * whole-solve CUDA graph. */
 typedef struct {
@@ -278,6 +279,18 @@ typedef struct {
 } amg_kernel_profile;
 int amg_profile_enable(amg_hierarchy *h, int enable);
 int amg_profile_read(const amg_hierarchy *h, amg_kernel_profile *out);
+
+/* Per-step breakdown: with amg_profile_enable(h, 2) every step of the solve
+ * phase (host-driven loop) is bracketed by CUDA events as well, and the
+ * device time and count of each step kind are summed into ms[256] and
+ * count[256], index 16 * level + role for the V-cycle steps of a level
+ * (role 0 pre-smoother, 1 residual, 2 restriction, 3 prolongation, 4 and 5
+ * the post-smoother's two steps) and 240 + k for the rest (k = 0 coarsest
+ * solve, 1 V-cycle input, 2 V-cycle output, 3 preconditioned-residual
+ * statistics, 4 search-direction update, 5 A p with p.Ap, 6 iterate and
+ * residual update).  Steps shorter than the host's launch rate read high.
+ * Switching profiling on from off resets these sums too. */
+int amg_profile_breakdown(const amg_hierarchy *h, double *ms, long long *count);
 
 /* ---- a12: time stepping (Eqs. 4-7 in coupled form) ------------------------
  * A simulation owns device state v, u_e, w (N each, zero at creation) and

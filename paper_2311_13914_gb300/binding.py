@@ -100,7 +100,7 @@ EXPORTS = (
     "amg_setup", "amg_setup_from_csr", "amg_num_levels", "amg_level_info", "amg_level_lanes",
     "amg_export_level",
     "amg_vcycle", "amg_solve", "amg_destroy", "amg_batch_create", "amg_batch_solve",
-    "amg_batch_destroy", "amg_profile_enable", "amg_profile_read",
+    "amg_batch_destroy", "amg_profile_enable", "amg_profile_read", "amg_profile_breakdown",
     "bd_sim_create", "bd_sim_set_state", "bd_sim_get_state", "bd_step", "bd_sim_destroy",
     "bd_elliptic_setup", "bd_dsim_create", "bd_dsim_set_state", "bd_dsim_get_state", "bd_dsim_step",
     "bd_dsim_destroy",
@@ -157,6 +157,7 @@ def lib():
             L.amg_batch_destroy.restype = None
             L.amg_profile_enable.argtypes = [_vp, C.c_int]
             L.amg_profile_read.argtypes = [_vp, _P(KernelProfile)]
+            L.amg_profile_breakdown.argtypes = [_vp, _P(C.c_double), _P(C.c_longlong)]
             L.amg_destroy.argtypes = [_vp]
             L.amg_destroy.restype = None
             L.bd_sim_create.argtypes = [_vp, _vp, _P(RmParams), _vp, C.c_int, C.c_double, _vp,
@@ -471,8 +472,26 @@ def amg_batch_solve(b: Batch, fs, xs, opts: SolveOptions | None = None, stream=N
     return [i.as_dict() for i in infos]
 
 
-def amg_profile_enable(h: Hierarchy, enable: bool = True):
+def amg_profile_enable(h: Hierarchy, enable: int = 1):
+    """0 off, 1 finest-operator timing, 2 also the per-step breakdown."""
     _check(lib().amg_profile_enable(h.ptr, int(enable)), "amg_profile_enable")
+
+
+PROFILE_ROLES = ("pre", "residual", "restrict", "prolong", "post1", "post2")
+PROFILE_STEPS = ("coarse", "vcycle_in", "vcycle_out", "z_stats", "p_update", "A_p", "x_r_update")
+
+
+def amg_profile_breakdown(h: Hierarchy) -> dict:
+    """{step name: (ms, count)} of the per-step breakdown (profiling level 2)."""
+    ms, cnt = (C.c_double * 256)(), (C.c_longlong * 256)()
+    _check(lib().amg_profile_breakdown(h.ptr, ms, cnt), "amg_profile_breakdown")
+    out = {}
+    for i in range(256):
+        if cnt[i]:
+            lv, role = divmod(i, 16)
+            name = PROFILE_STEPS[role] if lv == 15 else f"L{lv}_{PROFILE_ROLES[role]}"
+            out[name] = (ms[i], cnt[i])
+    return out
 
 
 def amg_profile_read(h: Hierarchy) -> dict:

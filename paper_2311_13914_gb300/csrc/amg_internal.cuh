@@ -81,6 +81,11 @@ struct amg_hierarchy {
     std::vector<double> ev_bytes, ev_flops;
     int ev_used = 0;
     amg_kernel_profile prof_sum{};
+    // per-step breakdown (profiling level 2): label of each event pair and the
+    // sums per label (level * 16 + role; level 15 holds the level-free steps)
+    std::vector<int> ev_label;
+    double trace_ms[256] = {};
+    long long trace_n[256] = {};
     ~amg_hierarchy() {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -103,7 +108,14 @@ int pcg_solve_begin(amg_hierarchy *h, const double *f_dev, double *x_dev, int wa
                     const solve_options *o, cudaStream_t s, solve_info *info, bool *pending);
 int pcg_solve_end(amg_hierarchy *h, cudaStream_t s, solve_info *info);
 int build_fine_sell(amg_hierarchy *h, const bd_system *sys, cudaStream_t s);
-int prof_begin(amg_hierarchy *h, cudaStream_t s);
+// Timed step of the solve phase (host-driven loop only).  `fine`: a
+// finest-operator application, timed at profiling level 1 and summed into
+// amg_kernel_profile; every labelled step is timed at level 2.
+enum ProfRole {
+    R_PRE = 0, R_RESID = 1, R_RESTRICT = 2, R_PROLONG = 3, R_POST1 = 4, R_POST2 = 5,
+    R_COARSE = 15 * 16, R_VIN, R_VOUT, R_ZSTATS, R_PUPDATE, R_AP, R_XRUPDATE
+};
+int prof_begin(amg_hierarchy *h, cudaStream_t s, int label, bool fine);
 void prof_end(amg_hierarchy *h, int slot, double bytes, double flops, cudaStream_t s);
 void prof_collect(amg_hierarchy *h);
 }  // namespace bd

@@ -493,24 +493,31 @@ static int apply_level(amg_hierarchy *h, int l, const LV<S> &lv, G g, E e, cudaS
 }
 
 // ------------------------------------------------------------------ live kernel timing
-int prof_begin(amg_hierarchy *h, cudaStream_t s)
+int prof_begin(amg_hierarchy *h, cudaStream_t s, int label, bool fine)
 {
-    if (!h->prof) return -1;
+    if (!h->prof || (!fine && h->prof < 2)) return -1;
     if (h->ev_used * 2 + 2 > (int)h->ev.size()) {
         if (h->ev.size() >= 8192) prof_collect(h);  // bounded pool: drain (synchronises)
         while (h->ev_used * 2 + 2 > (int)h->ev.size()) {
             cudaEvent_t e;
             if (cudaEventCreate(&e) != cudaSuccess) return -1;
             h->ev.push_back(e);
-            h->ev_bytes.push_back(0.0);
-            h->ev_flops.push_back(0.0);
+            if (h->ev.size() % 2 == 0) {
+                h->ev_bytes.push_back(0.0);
+                h->ev_flops.push_back(0.0);
+                h->ev_label.push_back(-1);
+            }
         }
     }
     int slot = h->ev_used++;
+    h->ev_bytes[slot] = 0.0;
+    h->ev_flops[slot] = 0.0;
+    h->ev_label[slot] = label;
     cudaEventRecord(h->ev[2 * slot], s);
     return slot;
 }
 
+// bytes/flops > 0 mark a finest-operator application (amg_kernel_profile sums)
 void prof_end(amg_hierarchy *h, int slot, double bytes, double flops, cudaStream_t s)
 {
     if (slot < 0) return;
@@ -524,11 +531,17 @@ void prof_collect(amg_hierarchy *h)
     for (int i = 0; i < h->ev_used; i++) {
         cudaEventSynchronize(h->ev[2 * i + 1]);
         float ms = 0.0f;
-        if (cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]) == cudaSuccess) {
+        if (cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]) != cudaSuccess) continue;
+        if (h->ev_bytes[i] > 0.0) {
             h->prof_sum.launches++;
             h->prof_sum.total_ms += ms;
             h->prof_sum.bytes += h->ev_bytes[i];
             h->prof_sum.flops += h->ev_flops[i];
+        }
+        const int lab = h->ev_label[i];
+        if (h->prof >= 2 && lab >= 0 && lab < 256) {
+            h->trace_ms[lab] += ms;
+            h->trace_n[lab]++;
         }
     }
     h->ev_used = 0;
@@ -686,21 +699,26 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
         v2<S> *u = l == 0 ? u0 : lv.u;
         v2<S> *d0 = lv.d;
         if (deg2) {
-            int sl = l == 0 ? prof_begin(h, s) : -1;
+            int sl = prof_begin(h, s, 16 * l + R_PRE, l == 0);
             BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{d0},
                                    EpiPre<S, SU>{f, lv.invd, d0, u, (S)L.ch_c1, (S)L.ch_c2}, s));
-            prof_end(h, sl, fine_bytes<S>(h, L, 4), fine_flops(h, L, SU), s);
+            prof_end(h, sl, l == 0 ? fine_bytes<S>(h, L, 4) : 0.0, fine_flops(h, L, SU), s);
         } else {
+            int sl = prof_begin(h, s, 16 * l + R_PRE, false);
             k_copy2<S><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, d0, u); ::bd::note_launch();
             BD_LAUNCH_CHECK();
+            prof_end(h, sl, 0.0, 0.0, s);
         }
-        int sr = l == 0 ? prof_begin(h, s) : -1;
+        int sr = prof_begin(h, s, 16 * l + R_RESID, l == 0);
         BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{u}, EpiResid<S>{f, lv.r}, s));
-        prof_end(h, sr, fine_bytes<S>(h, L, 3), fine_flops(h, L, SU), s);
+        prof_end(h, sr, l == 0 ? fine_bytes<S>(h, L, 3) : 0.0, fine_flops(h, L, SU), s);
         const Level &C = h->lev[l + 1];
         const LV<S> cv = view<S>(h, l + 1);
-        return launch_bsr<S>(L.R, lv.Rv, L.lanes[1], GatherVec<S>{lv.r},
-                             EpiStoreD0<S>{cv.f, cv.d, cv.invd, (S)C.ch_inv_theta}, s);
+        int sx = prof_begin(h, s, 16 * l + R_RESTRICT, false);
+        BD_TRY(launch_bsr<S>(L.R, lv.Rv, L.lanes[1], GatherVec<S>{lv.r},
+                             EpiStoreD0<S>{cv.f, cv.d, cv.invd, (S)C.ch_inv_theta}, s));
+        prof_end(h, sx, 0.0, 0.0, s);
+        return BD_OK;
     };
     auto up = [&](int l, auto su) -> int {
         constexpr bool SU = decltype(su)::value;
@@ -709,20 +727,24 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
         const v2<S> *f = l == 0 ? f0 : lv.f;
         v2<S> *u = l == 0 ? u0 : lv.u;
         const LV<S> cv = view<S>(h, l + 1);
+        int sp = prof_begin(h, s, 16 * l + R_PROLONG, false);
         BD_TRY(launch_bsr<S>(L.P, lv.Pv, L.lanes[2], GatherVec<S>{cv.u},
                              EpiAdd<S, SU>{u}, s));
-        int s1 = l == 0 ? prof_begin(h, s) : -1;
+        prof_end(h, sp, 0.0, 0.0, s);
+        int s1 = prof_begin(h, s, 16 * l + R_POST1, l == 0);
         BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{u},
                                EpiPost1<S, SU>{f, lv.invd, u, lv.r, lv.d, lv.w, (S)L.ch_inv_theta}, s));
-        prof_end(h, s1, fine_bytes<S>(h, L, 6), fine_flops(h, L, SU), s);
+        prof_end(h, s1, l == 0 ? fine_bytes<S>(h, L, 6) : 0.0, fine_flops(h, L, SU), s);
         if (deg2) {
-            int s2 = l == 0 ? prof_begin(h, s) : -1;
+            int s2 = prof_begin(h, s, 16 * l + R_POST2, l == 0);
             BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{lv.d},
                                    EpiPost2<S, SU>{lv.r, lv.d, lv.invd, lv.w, u, (S)L.ch_c1, (S)L.ch_c2}, s));
-            prof_end(h, s2, fine_bytes<S>(h, L, 5), fine_flops(h, L, SU), s);
+            prof_end(h, s2, l == 0 ? fine_bytes<S>(h, L, 5) : 0.0, fine_flops(h, L, SU), s);
         } else {
+            int s2 = prof_begin(h, s, 16 * l + R_POST2, false);
             k_copy2<S><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, lv.w, u); ::bd::note_launch();
             BD_LAUNCH_CHECK();
+            prof_end(h, s2, 0.0, 0.0, s);
         }
         return BD_OK;
     };
@@ -733,6 +755,7 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
         const S *f = (const S *)(nl == 1 ? f0 : cv.f);
         S *u = (S *)(nl == 1 ? u0 : cv.u);
         size_t smem = sizeof(double) * (size_t)h->nc;
+        int sc = prof_begin(h, s, R_COARSE, false);
         if (h->nc <= 256) {
             k_coarse_solve<S><<<1, 1024, smem, s>>>(h->nc, h->cinv.p, h->zc.p, h->zz, f, u); ::bd::note_launch();
         } else {
@@ -740,6 +763,7 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
             ::bd::note_launch();
         }
         BD_LAUNCH_CHECK();
+        prof_end(h, sc, 0.0, 0.0, s);
     }
     for (int l = nl - 2; l >= 0; l--)
         BD_TRY(l == 0 ? up(l, std::integral_constant<bool, SU0>{}) : up(l, std::false_type{}));
@@ -752,18 +776,23 @@ int vcycle_device(amg_hierarchy *h, const double *r_dev, double *z_dev, cudaStre
     Level &L0 = h->lev[0];
     if (h->prec32) {
         const LV<float> v0 = view<float>(h, 0);
+        int si = prof_begin(h, s, R_VIN, false);
         k_in32<<<grid_for(L0.N, 256), 256, 0, s>>>(L0.N, (const double2 *)r_dev, v0.invd,
                                                    (float)L0.ch_inv_theta, v0.f, v0.d); ::bd::note_launch();
         BD_LAUNCH_CHECK();
+        prof_end(h, si, 0.0, 0.0, s);
         BD_TRY((vcycle_impl<float, false>(h, v0.f, v0.u, s)));
+        int so = prof_begin(h, s, R_VOUT, false);
         k_out64<<<grid_for(L0.N, 256), 256, 0, s>>>(L0.N, v0.u, (double2 *)z_dev); ::bd::note_launch();
         BD_LAUNCH_CHECK();
+        prof_end(h, so, 0.0, 0.0, s);
         return BD_OK;
     }
     // FP64 sliced ELL: the finest level's gathered vectors in (v + u, u) form
     const LV<double> v0 = view<double>(h, 0);
     const bool su = h->sell.valid;
     if (h->nlev > 1) {
+        int si = prof_begin(h, s, R_VIN, false);
         if (su)
             k_scale_d0<double, true><<<grid_for(L0.N, 256), 256, 0, s>>>(L0.N, (const double2 *)r_dev, v0.invd,
                                                                          L0.ch_inv_theta, v0.d);
@@ -772,6 +801,7 @@ int vcycle_device(amg_hierarchy *h, const double *r_dev, double *z_dev, cudaStre
                                                                           L0.ch_inv_theta, v0.d);
         ::bd::note_launch();
         BD_LAUNCH_CHECK();
+        prof_end(h, si, 0.0, 0.0, s);
     }
     return su ? vcycle_impl<double, true>(h, (const double2 *)r_dev, (double2 *)z_dev, s)
               : vcycle_impl<double, false>(h, (const double2 *)r_dev, (double2 *)z_dev, s);
@@ -1403,12 +1433,20 @@ static int pcg_solve_loop(amg_hierarchy *h, const double *f_dev, double *x_dev, 
         status = BD_ENOTCONV;
         while (it < o->max_it) {
             BD_TRY(vcycle_device(h, (const double *)r, (double *)z, s));
+            int sz = prof_begin(h, s, R_ZSTATS, false);
             k_z_stats<<<G, 256, 0, s>>>(N, z, r, it == 0 ? nullptr : zold, make_fin(h, 3, it == 0)); ::bd::note_launch();
+            prof_end(h, sz, 0.0, 0.0, s);
+            int su = prof_begin(h, s, R_PUPDATE, false);
             p_update(h, N, z, p, zold, scal, it == 0, s);
-            int sq = h->prec32 ? -1 : prof_begin(h, s);
+            prof_end(h, su, 0.0, 0.0, s);
+            // the FP64 PCG operator counts among the finest-operator launches
+            // when the V-cycle is FP64 too (one kernel family per profile)
+            int sq = prof_begin(h, s, R_AP, !h->prec32);
             fine_reduce<0>(h, p, nullptr, q, make_fin(h, 4, 0), s);
-            prof_end(h, sq, fine_bytes<double>(h, L0, 2), fine_flops(h, L0, true), s);
+            prof_end(h, sq, h->prec32 ? 0.0 : fine_bytes<double>(h, L0, 2), fine_flops(h, L0, true), s);
+            int sx = prof_begin(h, s, R_XRUPDATE, false);
             xr_update(h, N, x, r, p, q, make_fin(h, 2, 0), s);
+            prof_end(h, sx, 0.0, 0.0, s);
             BD_LAUNCH_CHECK();
             BD_TRY(read_scal(h, s));
             it++;
@@ -1842,10 +1880,26 @@ extern "C" int amg_vcycle(amg_hierarchy *h, const double *r, double *z, int on_d
 
 extern "C" int amg_profile_enable(amg_hierarchy *h, int enable)
 {
-    if (!h) return BD_EINVAL;
+    if (!h || enable < 0 || enable > 2) return BD_EINVAL;
     prof_collect(h);
-    if (enable && !h->prof) h->prof_sum = amg_kernel_profile{};  // fresh sums when switched on
-    h->prof = enable ? 1 : 0;
+    if (enable && !h->prof) {  // fresh sums when switched on
+        h->prof_sum = amg_kernel_profile{};
+        for (int i = 0; i < 256; i++) {
+            h->trace_ms[i] = 0.0;
+            h->trace_n[i] = 0;
+        }
+    }
+    h->prof = enable;
+    return BD_OK;
+}
+
+extern "C" int amg_profile_breakdown(const amg_hierarchy *h, double *ms, long long *count)
+{
+    if (!h || !ms || !count) return BD_EINVAL;
+    for (int i = 0; i < 256; i++) {
+        ms[i] = h->trace_ms[i];
+        count[i] = h->trace_n[i];
+    }
     return BD_OK;
 }
 

@@ -304,6 +304,31 @@ def test_large_coarsest_level_matches_oracle(B, oracle_lib, m, limit):
     assert np.linalg.norm(xg - xo) <= 1e-7 * np.linalg.norm(xo)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_profile_breakdown_covers_the_solve(B, precision):
+    """Profiling level 2 times every solve-phase step: all V-cycle steps of
+    every level appear once per iteration, the PCG steps once per iteration,
+    and level 1 keeps its finest-operator sums."""
+    m = MESHES[0]
+    sysh = B.bd_assemble(m, W.DEFAULT_PARAMS, W.fibre_table(m))
+    h = B.amg_setup(sysh, B.amg_options_default(precision=precision))
+    nl = B.amg_num_levels(h)
+    f = W.rhs(2 * W.n_nodes(m), 1)
+    B.amg_profile_enable(h, 2)
+    _, info = B.amg_solve(h, f)
+    B.amg_profile_enable(h, 0)
+    it = info["iters"]
+    bd = B.amg_profile_breakdown(h)
+    for l in range(nl - 1):
+        for role in B.PROFILE_ROLES:
+            assert bd[f"L{l}_{role}"][1] == it
+    for step in ("coarse", "z_stats", "p_update", "A_p", "x_r_update"):
+        assert bd[step][1] == it
+    assert all(ms > 0.0 for ms, _ in bd.values())
+    prof = B.amg_profile_read(h)
+    assert prof["launches"] == it * (4 if precision else 5)
+
+
 def test_time_stepping_matches_oracle(B, oracle_lib):
     m = W.mesh(16, 16, 8, 0.6, 0.6, 0.3)
     p = W.DEFAULT_PARAMS
