@@ -99,6 +99,13 @@ def max_over_ranks(dist, value: float, use_cuda: bool) -> float:
     return float(t.item())
 
 
+def replica_throughput(world: int, steps: int, solves_per_step: int, elapsed_ms: float) -> float:
+    """Whole-job solves/s of N independent replicas (weak scaling): every rank
+    ran `steps` steps of `solves_per_step` solves; elapsed_ms is the maximum
+    over ranks of the timed region."""
+    return world * steps * solves_per_step / (elapsed_ms / 1e3)
+
+
 # ------------------------------------------------------------------ workload
 def workload(name):
     from paper_2311_13914_gb300 import workloads as W
@@ -304,7 +311,7 @@ def run_ours(args):
     launches = B.bd_launch_count() - launches0
     barrier(dist, local)
     elapsed_ms = max_over_ranks(dist, t0.elapsed_time(t1), True)
-    value = world * args.steps * T / (elapsed_ms / 1e3)
+    value = replica_throughput(world, args.steps, T, elapsed_ms)
 
     # untimed: per-step device time of the solve phase (host-driven loop with
     # CUDA events around every step), per PCG iteration
