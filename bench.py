@@ -377,7 +377,8 @@ def run_ours(args):
     t_hbm = rec["prof_bytes"] / (hbm_peak * 1e9)
     t_alu = rec["prof_flops"] / alu_peak
     per_launch = rec["prof_bytes"] / rec["prof_launches"] if rec["prof_launches"] else None
-    traffic = recorded_traffic(fp32)
+    # the recorded figure is for the 128x128x32 workload only
+    traffic = recorded_traffic(fp32) if args.workload == "paper" else None
     # the bound is whichever floor is higher for the flops the kernel executes
     # (FP64: 2 DFMA per stored node pair in the (v + u, u) form) and the
     # algorithmic bytes it must move
