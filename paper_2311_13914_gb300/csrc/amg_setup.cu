@@ -1014,6 +1014,11 @@ __global__ void k_fill(int n, double v, double *x)
 
 static inline int nblk(long long n, int b = 256) { return (int)((n + b - 1) / b); }
 
+// Thread block size of the one-thread-per-row setup kernels: on coarse levels
+// (few, long rows) one warp per block, so the rows spread over as many SMs as
+// possible instead of crowding a handful (each row is a sequential sum).
+static inline int row_block(long long rows) { return rows < (long long)kSM * 256 ? 32 : 256; }
+
 // ------------------------------------------------------------------ one level of Algorithm 1
 static int coarsen_level(amg_hierarchy *h, int l, bool &is_coarsest, cudaStream_t s)
 {
@@ -1038,14 +1043,15 @@ static int coarsen_level(amg_hierarchy *h, int l, bool &is_coarsest, cudaStream_
     DBuf<int> cnt;
     BD_TRY(cnt.alloc((size_t)N + 1));
     BD_TRY(S.rp.alloc((size_t)N + 1));
-    k_strength_count<<<nblk(N), 256, 0, s>>>(N, L.A.rp.p, L.A.ci.p, L.A.v.p, diag.p, o.theta, cnt.p); ::bd::note_launch();
+    k_strength_count<<<nblk(N, row_block(N)), row_block(N), 0, s>>>(N, L.A.rp.p, L.A.ci.p, L.A.v.p, diag.p, o.theta,
+                                                                   cnt.p); ::bd::note_launch();
     BD_LAUNCH_CHECK();
     long long snnz = 0;
     BD_TRY(exclusive_scan(cnt.p, S.rp.p, N, &snnz, s));
     S.nnz = snnz;
     BD_TRY(S.ci.alloc((size_t)snnz));
     BD_TRY(S.v.alloc((size_t)snnz));
-    k_strength_fill<<<nblk(N), 256, 0, s>>>(N, L.A.rp.p, L.A.ci.p, L.A.v.p, diag.p, o.theta, S.rp.p,
+    k_strength_fill<<<nblk(N, row_block(N)), row_block(N), 0, s>>>(N, L.A.rp.p, L.A.ci.p, L.A.v.p, diag.p, o.theta, S.rp.p,
                                             S.ci.p, S.v.p); ::bd::note_launch();
     BD_LAUNCH_CHECK();
     int hbad = 0;
@@ -1167,7 +1173,8 @@ static int coarsen_level(amg_hierarchy *h, int l, bool &is_coarsest, cudaStream_
     long long *acc = h->exact_acc.p;
     BD_TRY(exact_dot(vr.p, vz.p, n, &lst.p->rz, acc, s));
     for (int j = 0; j < o.esteig_steps; j++) {
-        k_spmv_ordered<<<nblk(N), 256, 0, s>>>(N, L.A.rp.p, L.A.ci.p, L.A.v.p, vp.p, vq.p); ::bd::note_launch();
+        k_spmv_ordered<<<nblk(N, row_block(N)), row_block(N), 0, s>>>(N, L.A.rp.p, L.A.ci.p, L.A.v.p, vp.p, vq.p);
+        ::bd::note_launch();
         BD_LAUNCH_CHECK();
         BD_TRY(exact_dot(vp.p, vq.p, n, &lst.p->pq, acc, s));
         k_lanczos_alpha<<<1, 1, 0, s>>>(lst.p, j); ::bd::note_launch();
