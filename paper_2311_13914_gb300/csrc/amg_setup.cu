@@ -931,11 +931,7 @@ __global__ void k_coarse_factor(int n, double *A, const double *__restrict__ z, 
 
 // Larger coarsest levels: the same rank-one-fixed matrix, inverted in place by
 // Gauss-Jordan elimination without pivoting (the matrix is symmetric positive
-// definite), one launch per pivot over the whole matrix (a thread block per
-// row segment, so the row's multiplier is one division per block).  Step k reads the
-// pivot row and column of the previous step from scratch buffers (double
-// buffered by the parity of k) and writes those of step k + 1, so no entry is
-// read after it is overwritten.
+// definite), in blocks of kGJ pivots (below).
 __global__ void k_coarse_stats(int n, const double *__restrict__ A, const double *__restrict__ z,
                                double *__restrict__ out)
 {
@@ -950,45 +946,107 @@ __global__ void k_coarse_stats(int n, const double *__restrict__ A, const double
     out[1] = zz;
 }
 
-// grid: x over columns (blockDim.x threads each), y over rows
+// one thread block per row, its threads strided over the columns
 __global__ void k_coarse_rank1(int n, double *__restrict__ A, const double *__restrict__ z,
-                               const double *__restrict__ st, double *__restrict__ row0, double *__restrict__ col0)
+                               const double *__restrict__ st)
 {
     const double smax = st[0], zz = st[1];
-    const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const size_t e = (size_t)i * n + j;
-    const double a = A[e] + (smax * z[i]) * z[j] / zz;
-    A[e] = a;
-    if (i == 0) row0[j] = a;
-    if (j == 0) col0[i] = a;
+    const int i = blockIdx.x;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const size_t e = (size_t)i * n + j;
+        A[e] = A[e] + (smax * z[i]) * z[j] / zz;
+    }
 }
 
-__global__ void k_gauss_jordan(int n, int k, double *__restrict__ A, const double *__restrict__ row,
-                               const double *__restrict__ col, double *__restrict__ nrow,
-                               double *__restrict__ ncol, int *__restrict__ bad)
+// Blocked Gauss-Jordan with pivot blocks of kGJ: for the pivot rows P,
+// D = A[P,P] is inverted in shared memory, W = D^-1 A[P,:], and every other row
+// i takes A[i,j] -= A[i,P] W[:,j] (a rank-kGJ update, FP64-bound, 32 rows per
+// thread block so each W value is reused 32 times), A[i,P] = -A[i,P] D^-1,
+// while the pivot rows become W with D^-1 in the pivot columns.
+constexpr int kGJ = 32;
+
+__global__ void k_gj_pivot(int n, int K, int bb, const double *__restrict__ A, double *__restrict__ Dinv,
+                           int *__restrict__ bad)
 {
-    const double piv = row[k];
-    const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
-    __shared__ double fi;  // col[i] / piv: one FP64 division per block, not per entry
-    if (threadIdx.x == 0) fi = col[i] / piv;
+    __shared__ double D[kGJ][kGJ + 1];
+    __shared__ double prow[kGJ], pcol[kGJ];
+    for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) D[e / bb][e % bb] = A[(size_t)(K + e / bb) * n + K + e % bb];
     __syncthreads();
-    if (j < n) {
-        const size_t e = (size_t)i * n + j;
-        double a;
-        if (i == k && j == k) {
-            if (!(piv > 0.0)) *bad = 1;
-            a = 1.0 / piv;
-        } else if (i == k) {
-            a = row[j] / piv;
-        } else if (j == k) {
-            a = -fi;
-        } else {
-            a = A[e] - fi * row[j];
+    for (int k = 0; k < bb; k++) {
+        const double piv = D[k][k];
+        if (threadIdx.x < bb) {
+            prow[threadIdx.x] = D[k][threadIdx.x];
+            pcol[threadIdx.x] = D[threadIdx.x][k];
         }
+        __syncthreads();
+        if (threadIdx.x == 0 && !(piv > 0.0)) *bad = 1;
+        for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) {
+            const int i = e / bb, j = e % bb;
+            double a;
+            if (i == k && j == k) a = 1.0 / piv;
+            else if (i == k) a = prow[j] / piv;
+            else if (j == k) a = -pcol[i] / piv;
+            else a = D[i][j] - pcol[i] / piv * prow[j];
+            D[i][j] = a;
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) Dinv[e] = D[e / bb][e % bb];
+}
+
+// W[k][j] = sum_m Dinv[k][m] A[K+m][j] for every column j (bb x n), and a copy
+// Cb of the pivot columns A[:, P] (the update overwrites them)
+__global__ void k_gj_panel(int n, int K, int bb, const double *__restrict__ A, const double *__restrict__ Dinv,
+                           double *__restrict__ W, double *__restrict__ Cb)
+{
+    __shared__ double Di[kGJ * kGJ];
+    for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) Di[e] = Dinv[e];
+    __syncthreads();
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    for (int m = 0; m < kGJ; m++) Cb[(size_t)j * kGJ + m] = m < bb ? A[(size_t)j * n + K + m] : 0.0;
+    double col[kGJ];
+#pragma unroll
+    for (int m = 0; m < kGJ; m++) col[m] = m < bb ? A[(size_t)(K + m) * n + j] : 0.0;
+    for (int k = 0; k < bb; k++) {
+        double w = 0.0;
+#pragma unroll
+        for (int m = 0; m < kGJ; m++)
+            if (m < bb) w = fma(Di[k * bb + m], col[m], w);
+        W[(size_t)k * n + j] = w;
+    }
+}
+
+// rows [32 blockIdx.y, +32), columns blockIdx.x * blockDim.x + threadIdx.x
+__global__ void k_gj_update(int n, int K, int bb, double *__restrict__ A, const double *__restrict__ Dinv,
+                            const double *__restrict__ W, const double *__restrict__ Cb)
+{
+    __shared__ double C[kGJ][kGJ];  // A[i, P] of the block's rows, from the copy
+    const int r0 = blockIdx.y * kGJ;
+    for (int e = threadIdx.x; e < kGJ * kGJ; e += blockDim.x) {
+        const int r = e / kGJ, m = e % kGJ;
+        C[r][m] = r0 + r < n ? Cb[(size_t)(r0 + r) * kGJ + m] : 0.0;
+    }
+    __syncthreads();
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const bool jp = j >= K && j < K + bb;
+    double w[kGJ];
+#pragma unroll
+    for (int m = 0; m < kGJ; m++)
+        w[m] = m < bb ? (jp ? Dinv[m * bb + (j - K)] : W[(size_t)m * n + j]) : 0.0;
+    for (int r = 0; r < kGJ; r++) {
+        const int i = r0 + r;
+        if (i >= n) break;
+        const size_t e = (size_t)i * n + j;
+        if (i >= K && i < K + bb) {       // pivot row: W, with D^-1 in the pivot columns
+            A[e] = w[i - K];
+            continue;
+        }
+        double a = jp ? 0.0 : A[e];
+#pragma unroll
+        for (int m = 0; m < kGJ; m++) a = fma(-C[r][m], w[m], a);
         A[e] = a;
-        if (i == k + 1) nrow[j] = a;
-        if (j == k + 1) ncol[i] = a;
     }
 }
 
@@ -1267,17 +1325,20 @@ static int build_coarsest(amg_hierarchy *h, int l, cudaStream_t s)
         k_coarse_factor<<<1, 256, 0, s>>>(n, Ad.p, h->zc.p, h->cinv.p, zz.p, bad.p); ::bd::note_launch();
         BD_LAUNCH_CHECK();
     } else {
-        DBuf<double> st, rows, cols;
+        DBuf<double> st;
         BD_TRY(st.alloc(2));
-        BD_TRY(rows.alloc(2 * (size_t)n));
-        BD_TRY(cols.alloc(2 * (size_t)n));
         k_coarse_stats<<<1, 32, 0, s>>>(n, Ad.p, h->zc.p, st.p); ::bd::note_launch();
-        const dim3 g((n + 127) / 128, n);
-        k_coarse_rank1<<<g, 128, 0, s>>>(n, Ad.p, h->zc.p, st.p, rows.p, cols.p); ::bd::note_launch();
-        for (int k = 0; k < n; k++) {
-            double *r0 = rows.p + (size_t)(k & 1) * n, *c0 = cols.p + (size_t)(k & 1) * n;
-            double *r1 = rows.p + (size_t)((k + 1) & 1) * n, *c1 = cols.p + (size_t)((k + 1) & 1) * n;
-            k_gauss_jordan<<<g, 128, 0, s>>>(n, k, Ad.p, r0, c0, r1, c1, bad.p); ::bd::note_launch();
+        k_coarse_rank1<<<n, 256, 0, s>>>(n, Ad.p, h->zc.p, st.p); ::bd::note_launch();
+        DBuf<double> Dinv, W, Cb;
+        BD_TRY(Dinv.alloc((size_t)kGJ * kGJ));
+        BD_TRY(W.alloc((size_t)kGJ * n));
+        BD_TRY(Cb.alloc((size_t)kGJ * n));
+        const dim3 gu((n + 127) / 128, (n + kGJ - 1) / kGJ);
+        for (int K = 0; K < n; K += kGJ) {
+            const int bb = std::min(kGJ, n - K);
+            k_gj_pivot<<<1, 256, 0, s>>>(n, K, bb, Ad.p, Dinv.p, bad.p); ::bd::note_launch();
+            k_gj_panel<<<(n + 127) / 128, 128, 0, s>>>(n, K, bb, Ad.p, Dinv.p, W.p, Cb.p); ::bd::note_launch();
+            k_gj_update<<<gu, 128, 0, s>>>(n, K, bb, Ad.p, Dinv.p, W.p, Cb.p); ::bd::note_launch();
         }
         BD_LAUNCH_CHECK();
         BD_CUDA(cudaMemcpyAsync(h->cinv.p, Ad.p, Ad.bytes(), cudaMemcpyDeviceToDevice, s));
