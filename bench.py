@@ -54,7 +54,11 @@ def parse_args(argv=None):
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="lanes per block row from the row-length rule instead of timing "
                          "the candidates at setup (amg_options.autotune = 0)")
-    ap.add_argument("--coarse-eq-limit", type=int, default=None)
+    ap.add_argument("--coarse-eq-limit", type=int, default=None,
+                    help="unknowns at which coarsening stops; default 2000 in the time-stepping "
+                         "mode (on this GPU a larger dense coarsest level, inverted once, pays off "
+                         "over the 100 solves of a simulation), the library default (Appendix A: "
+                         "100) in the other modes, whose slabs are small")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
                     help="fp32: FP32 V-cycle inside the FP64 flexible CG")
     ap.add_argument("--mode", choices=["step", "serve", "batch", "sweep"], default="step",
@@ -757,8 +761,13 @@ def run_sweep(args):
                        "sweep": rows}}
 
 
+STEP_COARSE_EQ_LIMIT = 2000  # time-stepping mode's coarsest level (see --coarse-eq-limit)
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.mode == "step" and args.coarse_eq_limit is None:
+        args.coarse_eq_limit = STEP_COARSE_EQ_LIMIT
     if args.mode == "serve":
         out = run_serve(args)
     elif args.mode == "batch":
