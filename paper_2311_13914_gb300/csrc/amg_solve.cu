@@ -605,12 +605,15 @@ __global__ void k_coarse_solve(int n, const double *__restrict__ cinv, const dou
 }
 
 // The same for larger coarsest levels, over the whole GPU: every block forms
-// z.r itself (same order in each, so all agree), then one warp per row.
+// z.r and the projected right-hand side r - (z.r/z.z) z in shared memory
+// itself (same order in each block, so all agree), then one warp per row: one
+// FP64 FMA per matrix entry.
 template <class S>
 __global__ void __launch_bounds__(256) k_coarse_solve_wide(int n, const double *__restrict__ cinv,
                                                            const double *__restrict__ z, double zz,
                                                            const S *__restrict__ r, S *__restrict__ x)
 {
+    extern __shared__ double rs[];
     __shared__ double red[8];
     __shared__ double alpha;
     double part = 0.0;
@@ -625,13 +628,15 @@ __global__ void __launch_bounds__(256) k_coarse_solve_wide(int n, const double *
     }
     __syncthreads();
     const double a = alpha;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) rs[i] = (double)r[i] - a * z[i];
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int nw = gridDim.x * (blockDim.x >> 5);
     for (int i = warp; i < n; i += nw) {
         const double *row = cinv + (size_t)i * n;
         double sacc = 0.0;
-        for (int j = lane; j < n; j += 32) sacc += row[j] * ((double)r[j] - a * z[j]);
+        for (int j = lane; j < n; j += 32) sacc = fma(row[j], rs[j], sacc);
         for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
         if (lane == 0) x[i] = (S)sacc;
     }
@@ -759,7 +764,7 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
         if (h->nc <= 256) {
             k_coarse_solve<S><<<1, 1024, smem, s>>>(h->nc, h->cinv.p, h->zc.p, h->zz, f, u); ::bd::note_launch();
         } else {
-            k_coarse_solve_wide<S><<<(h->nc + 7) / 8, 256, 0, s>>>(h->nc, h->cinv.p, h->zc.p, h->zz, f, u);
+            k_coarse_solve_wide<S><<<(h->nc + 7) / 8, 256, smem, s>>>(h->nc, h->cinv.p, h->zc.p, h->zz, f, u);
             ::bd::note_launch();
         }
         BD_LAUNCH_CHECK();
