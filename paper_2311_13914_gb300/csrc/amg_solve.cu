@@ -822,6 +822,10 @@ enum {
     S_NSLOTS
 };
 constexpr int kPart = 4;  // partial sums per block
+// Grid of the PCG vector kernels: one resident wave of fewer, larger blocks
+// than kRedBlocks, so the last block's reduction of the partials is shorter.
+constexpr int kVecBlocks = 608, kVecThreads = 512;
+constexpr int kMaxBlockThreads = 512;  // largest block of a reduction kernel
 
 // What the last block of a reduction kernel does with the totals.
 // first < 0: "first iteration" is read from the device iteration counter
@@ -909,7 +913,7 @@ __device__ void finish_stage(const Fin &f, double a, double b, double c, double 
 // tot[k].  That is 12 FP64 warp additions per value and block for 256 threads,
 // where a shuffle tree in every warp costs 45.
 template <int NV>
-__device__ __forceinline__ void block_sum(const double (&v)[4], double (*buf)[256], double *tot)
+__device__ __forceinline__ void block_sum(const double (&v)[4], double (*buf)[kMaxBlockThreads], double *tot)
 {
 #pragma unroll
     for (int k = 0; k < NV; k++) buf[k][threadIdx.x] = v[k];
@@ -928,11 +932,11 @@ __device__ __forceinline__ void block_sum(const double (&v)[4], double (*buf)[25
 // partials in a fixed order (independent of which block is last, so the
 // result is reproducible) and applies the stage.  No waiting: blocks that are
 // not last simply exit.  NV of (a, b, c, d) are live; the stage sees zeros for
-// the rest.  Needs blockDim.x <= 256 and a multiple of 32.
+// the rest.  Needs blockDim.x <= kMaxBlockThreads and a multiple of 32.
 template <int NV>
 __device__ void block_finish(double a, double b, double c, double d, const Fin &f)
 {
-    __shared__ double buf[NV][256];
+    __shared__ double buf[NV][kMaxBlockThreads];
     __shared__ double tot[4];
     __shared__ bool last;
     double v[4] = {a, b, c, d};
@@ -1190,16 +1194,16 @@ __global__ void k_project_x(int N, double2 *__restrict__ x, const double *__rest
 static void p_update(const amg_hierarchy *h, int N, double2 *z, double2 *p, double2 *zold, double *scal,
                      int first, cudaStream_t s)
 {
-    if (h->sell.valid) k_p_update<true><<<kRedBlocks, 256, 0, s>>>(N, z, p, zold, scal, first);
-    else k_p_update<false><<<kRedBlocks, 256, 0, s>>>(N, z, p, zold, scal, first);
+    if (h->sell.valid) k_p_update<true><<<kVecBlocks, kVecThreads, 0, s>>>(N, z, p, zold, scal, first);
+    else k_p_update<false><<<kVecBlocks, kVecThreads, 0, s>>>(N, z, p, zold, scal, first);
     note_launch();
 }
 
 static void xr_update(const amg_hierarchy *h, int N, double2 *x, double2 *r, const double2 *p,
                       const double2 *q, const Fin &fin, cudaStream_t s)
 {
-    if (h->sell.valid) k_xr_update<true><<<kRedBlocks, 256, 0, s>>>(N, x, r, p, q, fin);
-    else k_xr_update<false><<<kRedBlocks, 256, 0, s>>>(N, x, r, p, q, fin);
+    if (h->sell.valid) k_xr_update<true><<<kVecBlocks, kVecThreads, 0, s>>>(N, x, r, p, q, fin);
+    else k_xr_update<false><<<kVecBlocks, kVecThreads, 0, s>>>(N, x, r, p, q, fin);
     note_launch();
 }
 
@@ -1413,11 +1417,10 @@ static int pcg_solve_loop(amg_hierarchy *h, const double *f_dev, double *x_dev, 
     BD_CUDA(cudaEventCreate(&e1));
     BD_CUDA(cudaEventRecord(e0, s));
     BD_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * S_NSLOTS, s));
-    const int G = kRedBlocks;
-    k_f_stats<<<G, 256, 0, s>>>(N, (const double2 *)f_dev, make_fin(h, 0, 0)); ::bd::note_launch();
-    k_project_f<<<G, 256, 0, s>>>(N, (const double2 *)f_dev, fp, make_fin(h, 1, 0)); ::bd::note_launch();
+    k_f_stats<<<kVecBlocks, kVecThreads, 0, s>>>(N, (const double2 *)f_dev, make_fin(h, 0, 0)); ::bd::note_launch();
+    k_project_f<<<kVecBlocks, kVecThreads, 0, s>>>(N, (const double2 *)f_dev, fp, make_fin(h, 1, 0)); ::bd::note_launch();
     if (!warm) {
-        k_zero2<<<G, 256, 0, s>>>(N, x); ::bd::note_launch();
+        k_zero2<<<kVecBlocks, kVecThreads, 0, s>>>(N, x); ::bd::note_launch();
     }
     fine_reduce<1>(h, x, fp, r, make_fin(h, 2, 0), s);
     BD_LAUNCH_CHECK();
@@ -1431,7 +1434,7 @@ static int pcg_solve_loop(amg_hierarchy *h, const double *f_dev, double *x_dev, 
         if (null_part > 1e-8 * sqrt(ff)) status = BD_EINCONSISTENT;
     }
     if (status == BD_OK && nf == 0.0) {
-        k_zero2<<<G, 256, 0, s>>>(N, x); ::bd::note_launch();
+        k_zero2<<<kVecBlocks, kVecThreads, 0, s>>>(N, x); ::bd::note_launch();
         BD_LAUNCH_CHECK();
         rr = 0.0;
     } else if (status == BD_OK && !(rr <= o->rtol * nf)) {
@@ -1439,7 +1442,7 @@ static int pcg_solve_loop(amg_hierarchy *h, const double *f_dev, double *x_dev, 
         while (it < o->max_it) {
             BD_TRY(vcycle_device(h, (const double *)r, (double *)z, s));
             int sz = prof_begin(h, s, R_ZSTATS, false);
-            k_z_stats<<<G, 256, 0, s>>>(N, z, r, it == 0 ? nullptr : zold, make_fin(h, 3, it == 0)); ::bd::note_launch();
+            k_z_stats<<<kVecBlocks, kVecThreads, 0, s>>>(N, z, r, it == 0 ? nullptr : zold, make_fin(h, 3, it == 0)); ::bd::note_launch();
             prof_end(h, sz, 0.0, 0.0, s);
             int su = prof_begin(h, s, R_PUPDATE, false);
             p_update(h, N, z, p, zold, scal, it == 0, s);
@@ -1472,7 +1475,7 @@ static int pcg_solve_loop(amg_hierarchy *h, const double *f_dev, double *x_dev, 
     }
     // true residual and projection of x
     fine_reduce<1>(h, x, fp, nullptr, make_fin(h, 5, 0), s);
-    k_project_x<<<G, 256, 0, s>>>(N, x, scal); ::bd::note_launch();
+    k_project_x<<<kVecBlocks, kVecThreads, 0, s>>>(N, x, scal); ::bd::note_launch();
     BD_LAUNCH_CHECK();
     BD_CUDA(cudaEventRecord(e1, s));
     BD_TRY(read_scal(h, s));
@@ -1516,7 +1519,7 @@ static void end_capture_quietly(cudaStream_t s)
 static int capture_solve(amg_hierarchy *h, cudaStream_t s, cudaStream_t s2)
 {
     Level &L0 = h->lev[0];
-    const int N = L0.N, G = kRedBlocks;
+    const int N = L0.N;
     const bool flex = h->prec32;
     double2 *x = (double2 *)h->x.p, *r = (double2 *)h->r.p, *z = (double2 *)h->z.p;
     double2 *p = (double2 *)h->p.p, *q = (double2 *)h->q.p, *fp = (double2 *)h->fp.p;
@@ -1526,9 +1529,9 @@ static int capture_solve(amg_hierarchy *h, cudaStream_t s, cudaStream_t s2)
     // kernel-node counts per section (the launch counter counts executions, so
     // the increments made while capturing are taken back below)
     const long long c0 = launch_count();
-    k_f_stats<<<G, 256, 0, s>>>(N, fin, make_fin(h, 0, 0)); ::bd::note_launch();
-    k_project_f<<<G, 256, 0, s>>>(N, fin, fp, make_fin(h, 1, 0)); ::bd::note_launch();
-    k_zero_if<<<G, 256, 0, s>>>(N, x, scal, 0); ::bd::note_launch();
+    k_f_stats<<<kVecBlocks, kVecThreads, 0, s>>>(N, fin, make_fin(h, 0, 0)); ::bd::note_launch();
+    k_project_f<<<kVecBlocks, kVecThreads, 0, s>>>(N, fin, fp, make_fin(h, 1, 0)); ::bd::note_launch();
+    k_zero_if<<<kVecBlocks, kVecThreads, 0, s>>>(N, x, scal, 0); ::bd::note_launch();
     BD_LAUNCH_CHECK();
     cudaStreamCaptureStatus cs;
     cudaGraph_t g = nullptr;
@@ -1551,7 +1554,7 @@ static int capture_solve(amg_hierarchy *h, cudaStream_t s, cudaStream_t s2)
     const long long c1 = launch_count();
     BD_CUDA(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     BD_TRY(vcycle_device(h, (const double *)r, (double *)z, s2));
-    k_z_stats<<<G, 256, 0, s2>>>(N, z, r, zold, make_fin(h, 3, -1)); ::bd::note_launch();
+    k_z_stats<<<kVecBlocks, kVecThreads, 0, s2>>>(N, z, r, zold, make_fin(h, 3, -1)); ::bd::note_launch();
     p_update(h, N, z, p, zold, scal, -1, s2);
     fine_reduce<0>(h, p, nullptr, q, make_fin(h, 4, 0), s2);
     xr_update(h, N, x, r, p, q, make_fin(h, 7, 0, cond), s2);
@@ -1560,9 +1563,9 @@ static int capture_solve(amg_hierarchy *h, cudaStream_t s, cudaStream_t s2)
     BD_CUDA(cudaStreamEndCapture(s2, &body_out));
     const long long c2 = launch_count();
     BD_CUDA(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
-    k_zero_if<<<G, 256, 0, s>>>(N, x, scal, 1); ::bd::note_launch();
+    k_zero_if<<<kVecBlocks, kVecThreads, 0, s>>>(N, x, scal, 1); ::bd::note_launch();
     fine_reduce<1>(h, x, fp, nullptr, make_fin(h, 5, 0), s);
-    k_project_x<<<G, 256, 0, s>>>(N, x, scal); ::bd::note_launch();
+    k_project_x<<<kVecBlocks, kVecThreads, 0, s>>>(N, x, scal); ::bd::note_launch();
     BD_LAUNCH_CHECK();
     const long long c3 = launch_count();
     h->graph_pre = c1 - c0;
