@@ -1243,16 +1243,23 @@ static int tune_operator(const BSR &M, const S *vals, const v2<S> *x, const v2<S
             BD_CUDA(cudaEventRecord(ev[c][k][1], s));
         }
     BD_CUDA(cudaStreamSynchronize(s));
-    float best = 0.0f;
+    // the fastest median wins unless the row-length rule's count (*lanes on
+    // entry, when among the candidates) is within 3 % of it: near-ties then
+    // resolve the same way on every run
+    const int rule = *lanes;
+    float best = 0.0f, t_rule = -1.0f;
+    int bestT = rule;
     for (int c = 0; c < nc; c++) {
         float t[kLaneReps];
         for (int k = 0; k < kLaneReps; k++) BD_CUDA(cudaEventElapsedTime(&t[k], ev[c][k][0], ev[c][k][1]));
         const float med = std::max(std::min(t[0], t[1]), std::min(std::max(t[0], t[1]), t[2]));
+        if (cand[c] == rule) t_rule = med;
         if (c == 0 || med < best) {
             best = med;
-            *lanes = cand[c];
+            bestT = cand[c];
         }
     }
+    *lanes = (t_rule >= 0.0f && t_rule <= 1.03f * best) ? rule : bestT;
     return BD_OK;
 }
 
