@@ -51,6 +51,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-sample-steps", type=int, default=2)
     ap.add_argument("--square-levels", type=int, default=None)
     ap.add_argument("--theta", type=float, default=None)
+    ap.add_argument("--no-fp32-form", action="store_true",
+                    help="skip the untimed side measurement of the FP32 V-cycle form")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="lanes per block row from the row-length rule instead of timing "
                          "the candidates at setup (amg_options.autotune = 0)")
@@ -317,6 +319,38 @@ def run_ours(args):
     elapsed_ms = max_over_ranks(dist, t0.elapsed_time(t1), True)
     value = replica_throughput(world, args.steps, T, elapsed_ms)
 
+    # the precision form beside the FP64 line (same workload and protocol,
+    # FP32 V-cycle inside the FP64 flexible CG; rank 0, after the timed region)
+    fp32_form = None
+    if rank == 0 and args.precision == "fp64" and not args.no_fp32_form:
+        a32 = argparse.Namespace(**{**vars(args), "precision": "fp32"})
+        opts32 = amg_opts(B, a32)
+
+        def step32():
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            sh = B.bd_assemble(mesh, p, fib_d, stream=stream)
+            hh = B.amg_setup(sh, opts32, stream=stream)
+            e[1].record(stream)
+            sm = B.bd_sim_create(sh, hh, stim=stim_d, stim_ms=STIM_MS, stream=stream)
+            inf = B.bd_step(sm, T, stream=stream)
+            e[2].record(stream)
+            stream.synchronize()
+            out = (e[0].elapsed_time(e[2]), e[1].elapsed_time(e[2]), inf)
+            sm.close()
+            hh.close()
+            sh.close()
+            return out
+
+        step32()
+        runs = [step32() for _ in range(max(1, min(args.steps, 2)))]
+        ms_step = statistics.mean(r[0] for r in runs)
+        fp32_form = {"value": T / (ms_step / 1e3), "unit": "solves/s",
+                     "solve_only_solves_per_s": T / (statistics.mean(r[1] for r in runs) / 1e3),
+                     "mean_pcg_iters": statistics.mean(r[2]["total_iters"] / T for r in runs),
+                     "max_true_rel_res": max(r[2]["true_rel_res"] for r in runs),
+                     "steps": len(runs), "dtype": "f64 CG, FP32 V-cycle"}
+
     # untimed: per-step device time of the solve phase (host-driven loop with
     # CUDA events around every step), per PCG iteration
     breakdown = None
@@ -420,6 +454,7 @@ def run_ours(args):
                    "levels": rec.get("levels"), "operator_complexity": rec.get("op_complexity"),
                    "lanes_A_R_P": rec.get("lanes"),
                    "breakdown_us_per_pcg_iteration": breakdown,
+                   "fp32_vcycle_form": fp32_form,
                    "amg_options": {k: getattr(amg_opts(B, args), k) for k in
                                    ("theta", "square_levels", "coarse_eq_limit", "cheb_degree",
                                     "precision", "autotune")}},
