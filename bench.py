@@ -53,9 +53,15 @@ def parse_args(argv=None):
     ap.add_argument("--theta", type=float, default=None)
     ap.add_argument("--no-fp32-form", action="store_true",
                     help="skip the untimed side measurement of the FP32 V-cycle form")
-    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
-                    help="lanes per block row from the row-length rule instead of timing "
-                         "the candidates at setup (amg_options.autotune = 0)")
+    ap.add_argument("--autotune", type=int, choices=(0, 1), default=None,
+                    help="1: time the candidate forms of the block operators at setup "
+                         "(amg_options.autotune = 1); 0: the row-count and row-length rule.  "
+                         "Default 0 in the time-stepping mode (the rule matched the fastest "
+                         "form inside the V-cycle on every operator of the 128x128x32 slab, "
+                         "while single-launch timings misranked one, and setup is inside the "
+                         "timed step), 1 in the other modes")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_const", const=0,
+                    help="same as --autotune 0")
     ap.add_argument("--coarse-eq-limit", type=int, default=None,
                     help="unknowns at which coarsening stops; default 2000 in the time-stepping "
                          "mode (on this GPU a larger dense coarsest level, inverted once, pays off "
@@ -803,6 +809,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.mode == "step" and args.coarse_eq_limit is None:
         args.coarse_eq_limit = STEP_COARSE_EQ_LIMIT
+    if args.autotune is None:
+        args.autotune = 0 if args.mode == "step" else 1
     if args.mode == "serve":
         out = run_serve(args)
     elif args.mode == "batch":

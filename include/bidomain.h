@@ -81,12 +81,12 @@ typedef struct {
     int precision;         /* 0: FP64 V-cycle; 1: FP32 V-cycle (values and vectors
                               of every level in FP32, coarsest solve in FP64) inside
                               an FP64 flexible CG (Polak-Ribiere beta) (0)          */
-    int autotune;          /* 0: lanes per block row of the V-cycle's block-CSR
-                              operators from a row-length rule; 1: amg_setup times
-                              the candidates of every operator of at least 20000
-                              blocks on this GPU (cold L2, median of three) and
-                              keeps the fastest; it needs a 192 MB scratch buffer
-                              for a moment and keeps the rule without one.
+    int autotune;          /* 0: form of the V-cycle's block operators (see
+                              amg_level_lanes) from a row-count and row-length
+                              rule; 1: amg_setup times the candidate forms of
+                              every operator of at least 20000 blocks on this
+                              GPU (warm, median of three) and keeps the
+                              fastest unless the rule's form is within 3 %.
                               Either way the choice is fixed per hierarchy, so its
                               solves are reproducible; the two choices differ in
                               the summation order of row sums (last bits) (0)       */
@@ -199,11 +199,28 @@ int amg_num_levels(const amg_hierarchy *h, int *nlevels);
 int amg_level_info(const amg_hierarchy *h, int level, int *n, long long *nnz, int *n_agg,
                    double *lambda, long long *p_nnz);
 
-/* Lanes per block row the V-cycle uses on level `level` for A_l, R_l and P_l
- * (lanes[0..2]; 0 where the operator is not applied in block-CSR form: A on a
- * sliced-ELL finest level, A on the coarsest, R and P on the coarsest).
- * 64, 128 or 256 mean one thread block of that size per row. */
+/* Form in which the V-cycle applies A_l, R_l and P_l on level `level`
+ * (lanes[0..2]):
+ *   T = 1..32       block-CSR, T lanes per 2x2-block row (a butterfly sums them);
+ *   T = 64..256     block-CSR, one thread block of T threads per row;
+ *   T = -K (K = 1, 2, 4, 8)  sliced: rows sorted by block count (descending,
+ *                   stable) within windows of 1024 rows, 32/K rows per warp,
+ *                   K lanes per row, entries stored group-major so every load
+ *                   of a warp is contiguous; it gives the same bits as T = K;
+ *   0               not applied in block form (A on a sliced-ELL finest level,
+ *                   everything on the coarsest level, solved densely).
+ * The sliced form is never used for A on the finest level. */
 int amg_level_lanes(const amg_hierarchy *h, int level, int lanes[3]);
+
+/* Override the forms chosen by amg_setup (values as amg_level_lanes returns
+ * them; 0 keeps an operator's current form).  Builds the sliced forms it
+ * needs in the V-cycle's precision and drops the hierarchy's captured solve
+ * graph (the next solve captures it anew).  No solve with h may be in flight
+ * on any stream; synchronises `stream`.  Errors: BD_EINVAL (NULL, level out
+ * of range, a value not listed above, a nonzero value for an operator the
+ * level does not apply in block form, or a sliced form for A on the finest
+ * level), BD_ESTATE (a batch of amg_batch_create holds h), BD_ENOMEM, BD_ECUDA. */
+int amg_set_level_lanes(amg_hierarchy *h, int level, const int lanes[3], void *stream);
 
 /* Copy level data to HOST arrays (sizes from amg_level_info; any pointer may
  * be NULL): A_l as scalar CSR, MIS flags and aggregate ids per node, P_l as
@@ -242,7 +259,8 @@ void amg_destroy(amg_hierarchy *h);
  * amg_batch_create: h[0..count-1] distinct hierarchies (each one's buffers
  *   serve one branch; BD_EINVAL on a repeat).  The batch does not own them;
  *   destroy the batch before any of them, and use none of them elsewhere while
- *   a batch solve runs.
+ *   a batch solve runs.  While the batch exists amg_set_level_lanes refuses
+ *   its hierarchies (BD_ESTATE).
  * amg_batch_solve: f[k], x[k]: DEVICE pointers to 2 n_k doubles each (f_k
  *   right-hand side; x_k initial guess if opts->warm_start, solution out),
  *   valid on `stream`.  One solve_options for all (strict mode is not

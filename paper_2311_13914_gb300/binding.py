@@ -98,7 +98,7 @@ EXPORTS = (
     "amg_options_default", "solve_options_default", "bd_rm_params_default",
     "bd_assemble", "bd_system_info", "bd_system_export", "bd_system_destroy",
     "amg_setup", "amg_setup_from_csr", "amg_num_levels", "amg_level_info", "amg_level_lanes",
-    "amg_export_level",
+    "amg_set_level_lanes", "amg_export_level",
     "amg_vcycle", "amg_solve", "amg_destroy", "amg_batch_create", "amg_batch_solve",
     "amg_batch_destroy", "amg_profile_enable", "amg_profile_read", "amg_profile_breakdown",
     "bd_sim_create", "bd_sim_set_state", "bd_sim_get_state", "bd_step", "bd_sim_destroy",
@@ -148,6 +148,7 @@ def lib():
             L.amg_level_info.argtypes = [_vp, C.c_int, _P(C.c_int), _P(C.c_longlong),
                                          _P(C.c_int), _P(C.c_double), _P(C.c_longlong)]
             L.amg_level_lanes.argtypes = [_vp, C.c_int, _P(C.c_int)]
+            L.amg_set_level_lanes.argtypes = [_vp, C.c_int, _P(C.c_int), _vp]
             L.amg_export_level.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
             L.amg_vcycle.argtypes = [_vp, _vp, _vp, C.c_int, _vp]
             L.amg_solve.argtypes = [_vp, _vp, _vp, C.c_int, _P(SolveOptions), _vp, _P(SolveInfo)]
@@ -379,10 +380,18 @@ def amg_level_info(h: Hierarchy, level: int) -> dict:
 
 
 def amg_level_lanes(h: Hierarchy, level: int) -> tuple:
-    """Lanes per block row of A_l, R_l, P_l in the V-cycle (0: not block CSR)."""
+    """Form of A_l, R_l, P_l in the V-cycle: T > 0 block CSR with T lanes per
+    row, -K the sliced form with K lanes per row, 0 not applied in block form."""
     lanes = (C.c_int * 3)()
     _check(lib().amg_level_lanes(h.ptr, level, lanes), "amg_level_lanes")
     return tuple(lanes)
+
+
+def amg_set_level_lanes(h: Hierarchy, level: int, lanes, stream=None) -> None:
+    """Override the forms of A_l, R_l, P_l (values as amg_level_lanes gives
+    them, 0 keeps one)."""
+    arr = (C.c_int * 3)(*[int(t) for t in lanes])
+    _check(lib().amg_set_level_lanes(h.ptr, level, arr, _stream(stream)), "amg_set_level_lanes")
 
 
 def amg_export_level(h: Hierarchy, level: int, stream=None) -> dict:

@@ -9,6 +9,29 @@ constexpr int kMaxLevels = 16;
 constexpr int kMaxCoarse = 4096;   // unknowns of the dense coarsest level
 constexpr int kRedBlocks = 1216;   // blocks of the solve's reduction kernels (8 x SMs)
 
+// A block-CSR operator of the V-cycle in sliced form: rows sorted by block
+// count (descending, ties by row) within windows of kSliceWindow rows, slices
+// of 32/K consecutive sorted rows, K lanes per row.  Group g of a slice holds
+// entries gK .. gK+K-1 of each of its rows in 32 consecutive positions (lane
+// i K + k: entry g K + k of the slice's row i), so every group is one
+// coalesced load per warp and all lanes of a row-slice run the same trip
+// count.  Positions past a row's end hold column 0 with zero values.
+constexpr int kSliceWindow = 1024;
+struct SlicedOp {
+    int K = 0;                  // lanes per row (0: not built)
+    int rows = 0;               // block rows
+    int nsl = 0;                // slices
+    long long groups = 0;       // 32-entry groups
+    int warps = 0;              // warps of the launch (grid x 8)
+    DBuf<int> order;            // rows padded to 32: row at each sorted position, -1 past the end
+    DBuf<int> sptr;             // nsl + 1: first group of each slice
+    DBuf<int> wsl;              // warps + 1: first slice of each warp (balanced by groups)
+    DBuf<int> cnt;              // nsl: groups per slice (build scratch)
+    DBuf<int> col;              // groups * 32 block columns
+    DBuf<double> v;             // FP64: groups * 32 (a00, a01) pairs, then as many (a10, a11)
+    DBuf<float> v32;            // FP32: groups * 32 float4 (a00, a01, a10, a11)
+};
+
 struct Level {
     int N = 0;                 // nodes (unknowns 2N)
     BSR A;                     // operator
@@ -26,8 +49,11 @@ struct Level {
     DBuf<float> f32, u32, r32, d32, w32;
     // Chebyshev coefficients (host copies)
     double ch_inv_theta = 0, ch_c1 = 0, ch_c2 = 0;
-    // lanes per block row of A, R and P in the V-cycle's precision
+    // lanes per block row of A, R and P in the V-cycle's precision: T > 0
+    // block-CSR with T lanes (64..256: a thread block per row), -K the
+    // sliced form sl[op] with K lanes per row
     int lanes[3] = {0, 0, 0};
+    SlicedOp sl[3];
 };
 
 // Finest level in sliced-ELL form (32 rows per slice, slot-major), using the
@@ -86,6 +112,7 @@ struct amg_hierarchy {
     std::vector<int> ev_label;
     double trace_ms[256] = {};
     long long trace_n[256] = {};
+    int batch_refs = 0;         // batches holding graphs of this hierarchy's kernels
     ~amg_hierarchy() {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
         if (graph_exec) cudaGraphExecDestroy(graph_exec);

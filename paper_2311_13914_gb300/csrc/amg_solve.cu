@@ -124,6 +124,146 @@ __global__ void __launch_bounds__(TB) k_bsr_wide(int N, const int *__restrict__ 
     }
 }
 
+// ------------------------------------------------------------------ sliced block operator
+// FP64 values sit in two planes, (a00, a01) then (a10, a11), so each half of a
+// group is one contiguous 512-byte warp load; FP32 values are one float4.
+__device__ __forceinline__ BlkS<double> load_sliced(const double *__restrict__ v, size_t idx, size_t plane)
+{
+    const double2 p = ((const double2 *)v)[idx], q = ((const double2 *)v)[plane + idx];
+    return {p.x, p.y, q.x, q.y};
+}
+__device__ __forceinline__ BlkS<float> load_sliced(const float *__restrict__ v, size_t idx, size_t)
+{
+    const float4 p = ((const float4 *)v)[idx];
+    return {p.x, p.y, p.z, p.w};
+}
+
+// One warp per slice of 32/K rows with K lanes each; warp w takes slices
+// [wsl[w], wsl[w+1]), which split the groups evenly over the warps.  Lane k of
+// a row sums entries k, k+K, ... and the K partial sums meet in a butterfly,
+// the order k_bsr<K> uses, so both forms give the same bits.  Rows sorted by
+// length leave few padded positions, and every FP64 instruction of the loop
+// and the epilogue works on 32 lanes (the FP64 pipe, not HBM, bounds the
+// coarse levels in FP64).
+template <int K, class S, class G, class E, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_bsell(const int *__restrict__ sptr, const int *__restrict__ wsl,
+                                                    const int *__restrict__ order, const int *__restrict__ col,
+                                                    const S *__restrict__ v, size_t plane, G gather, E epi)
+{
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int s1 = wsl[w + 1];
+    for (int sl = wsl[w]; sl < s1; sl++) {
+        const int j1 = sptr[sl + 1];
+        S y0 = 0, y1 = 0;
+#pragma unroll 4
+        for (int j = sptr[sl]; j < j1; j++) {
+            const size_t idx = (size_t)j * 32 + lane;
+            const int q = col[idx];
+            const BlkS<S> a = load_sliced(v, idx, plane);
+            const v2<S> x = gather(q);
+            y0 = fma(a.a00, x.x, fma(a.a01, x.y, y0));
+            y1 = fma(a.a10, x.x, fma(a.a11, x.y, y1));
+        }
+#pragma unroll
+        for (int o = K / 2; o > 0; o >>= 1) {
+            y0 += __shfl_xor_sync(0xffffffffu, y0, o, K);
+            y1 += __shfl_xor_sync(0xffffffffu, y1, o, K);
+        }
+        if ((lane & (K - 1)) == 0) {
+            const int r = order[sl * (32 / K) + lane / K];
+            if (r >= 0) epi(r, y0, y1);
+        }
+    }
+}
+
+// Sorted position of every row of a window: by block count, descending, ties
+// by row (a stable, deterministic order).  One thread block per window.
+__global__ void k_slice_order(int rows, const int *__restrict__ rp, int *__restrict__ order)
+{
+    __shared__ int len[kSliceWindow];
+    const int w0 = blockIdx.x * kSliceWindow;
+    const int n = min(kSliceWindow, rows - w0);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) len[i] = rp[w0 + i + 1] - rp[w0 + i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int li = len[i];
+        int rank = 0;
+        for (int j = 0; j < n; j++) {
+            const int lj = len[j];
+            rank += (lj > li) || (lj == li && j < i);
+        }
+        order[w0 + rank] = w0 + i;
+    }
+}
+
+// groups of slice sl: its longest row's block count over K, rounded up
+__global__ void k_slice_groups(int nsl, int K, const int *__restrict__ rp, const int *__restrict__ order,
+                               int *__restrict__ cnt)
+{
+    const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl >= nsl) return;
+    const int H = 32 / K;
+    int mx = 0;
+    for (int i = 0; i < H; i++) {
+        const int r = order[sl * H + i];
+        if (r >= 0) mx = max(mx, rp[r + 1] - rp[r]);
+    }
+    cnt[sl] = (mx + K - 1) / K;
+}
+
+__device__ __forceinline__ void store_sliced(double *v, size_t idx, size_t plane, const double *a, bool in)
+{
+    ((double2 *)v)[idx] = in ? make_double2(a[0], a[1]) : make_double2(0.0, 0.0);
+    ((double2 *)v)[plane + idx] = in ? make_double2(a[2], a[3]) : make_double2(0.0, 0.0);
+}
+__device__ __forceinline__ void store_sliced(float *v, size_t idx, size_t, const double *a, bool in)
+{
+    ((float4 *)v)[idx] = in ? make_float4((float)a[0], (float)a[1], (float)a[2], (float)a[3])
+                            : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+// one thread per (slice, lane): the entries of its row it owns, group by group
+template <class S>
+__global__ void k_slice_fill(int nsl, int K, const int *__restrict__ rp, const int *__restrict__ ci,
+                             const double *__restrict__ bv, const int *__restrict__ order,
+                             const int *__restrict__ sptr, int *__restrict__ col, S *__restrict__ v, size_t plane)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)nsl * 32) return;
+    const int sl = (int)(t >> 5), lane = (int)(t & 31);
+    const int r = order[sl * (32 / K) + lane / K], k = lane % K;
+    const int b = r >= 0 ? rp[r] : 0, len = r >= 0 ? rp[r + 1] - b : 0;
+    const int g0 = sptr[sl], g1 = sptr[sl + 1];
+    for (int g = g0; g < g1; g++) {
+        const int j = (g - g0) * K + k;
+        const size_t idx = (size_t)g * 32 + lane;
+        const bool in = j < len;
+        col[idx] = in ? ci[b + j] : 0;
+        store_sliced(v, idx, plane, bv + 4 * (size_t)(in ? b + j : 0), in);
+    }
+}
+
+// first slice of every warp: the lower bound of w * groups / warps in sptr
+__global__ void k_slice_warps(int nsl, long long groups, int warps, const int *__restrict__ sptr,
+                              int *__restrict__ wsl)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w > warps) return;
+    if (w == warps) {
+        wsl[w] = nsl;
+        return;
+    }
+    const long long g = groups * w / warps;
+    int lo = 0, hi = nsl;
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (sptr[m] < g) lo = m + 1;
+        else hi = m;
+    }
+    wsl[w] = lo;
+}
+
 // ------------------------------------------------------------------ finest level, sliced ELL
 // Block b's share [share_lo(n), share_hi(n)) of n rows or nodes: the grid
 // splits the 32-row slices in equal contiguous parts, so with one resident
@@ -362,24 +502,146 @@ static int launch_bsr(const BSR &A, const S *vals, int T, G g, E e, cudaStream_t
     return BD_OK;
 }
 
-// Lanes per block row.  Every lane-level reduction step costs adds, which are
-// scarce in FP64 on this part, so FP64 rows use as few lanes as their length
-// allows (one thread per row for short rows).  FP32 adds are cheap, so FP32
-// rows use more lanes to shorten each thread's chain of dependent loads.
-// Levels with few, long rows (the dense-ish coarse levels) take a whole thread
-// block per row; small levels get more lanes so the grid still fills the GPU.
+template <class S> static const S *sliced_vals(const SlicedOp &o);
+template <> const double *sliced_vals<double>(const SlicedOp &o) { return o.v.p; }
+template <> const float *sliced_vals<float>(const SlicedOp &o) { return o.v32.p; }
+
+template <class S, class G, class E>
+static int launch_sliced(const SlicedOp &o, int K, G g, E e, cudaStream_t s)
+{
+    if (o.K != K || !sliced_vals<S>(o)) return BD_ESTATE;
+    constexpr int MB = sizeof(S) == 8 ? 4 : 8;  // as the finest level's sliced ELL
+    const S *v = sliced_vals<S>(o);
+    const size_t plane = (size_t)o.groups * 32;
+    const int grid = o.warps / 8;
+    switch (K) {
+    case 1: k_bsell<1, S, G, E, MB><<<grid, 256, 0, s>>>(o.sptr.p, o.wsl.p, o.order.p, o.col.p, v, plane, g, e); break;
+    case 2: k_bsell<2, S, G, E, MB><<<grid, 256, 0, s>>>(o.sptr.p, o.wsl.p, o.order.p, o.col.p, v, plane, g, e); break;
+    case 4: k_bsell<4, S, G, E, MB><<<grid, 256, 0, s>>>(o.sptr.p, o.wsl.p, o.order.p, o.col.p, v, plane, g, e); break;
+    default: k_bsell<8, S, G, E, MB><<<grid, 256, 0, s>>>(o.sptr.p, o.wsl.p, o.order.p, o.col.p, v, plane, g, e); break;
+    }
+    ::bd::note_launch();
+    BD_LAUNCH_CHECK();
+    return BD_OK;
+}
+
+static bool sliced_k_ok(int K) { return K == 1 || K == 2 || K == 4 || K == 8; }
+
+// Build M's sliced form with K lanes per row in the V-cycle's precision (the
+// sorted row order is kept across rebuilds of the same operator, and buffers
+// large enough already are reused).  Stream-ordered on s.
+template <class T> static int ensure(DBuf<T> &b, size_t n)
+{
+    return b.p && b.n >= n ? BD_OK : b.alloc(n);
+}
+
+static int build_sliced(const BSR &M, int K, bool fp32, SlicedOp &o, cudaStream_t s)
+{
+    if (M.nbr <= 0 || M.nb <= 0 || !sliced_k_ok(K)) return BD_EINVAL;
+    const int rows = M.nbr, H = 32 / K;
+    o.K = 0;
+    if (o.rows != rows || !o.order.p) {
+        const size_t padded = ((size_t)rows + 31) / 32 * 32;
+        BD_TRY(o.order.alloc(padded));
+        BD_CUDA(cudaMemsetAsync(o.order.p, 0xff, sizeof(int) * padded, s));  // -1 past the last row
+        k_slice_order<<<(rows + kSliceWindow - 1) / kSliceWindow, 256, 0, s>>>(rows, M.rp.p, o.order.p);
+        ::bd::note_launch();
+        BD_LAUNCH_CHECK();
+        o.rows = rows;
+    }
+    o.nsl = (rows + H - 1) / H;
+    BD_TRY(ensure(o.cnt, (size_t)o.nsl));
+    BD_TRY(ensure(o.sptr, (size_t)o.nsl + 1));
+    k_slice_groups<<<(o.nsl + 255) / 256, 256, 0, s>>>(o.nsl, K, M.rp.p, o.order.p, o.cnt.p);
+    ::bd::note_launch();
+    BD_LAUNCH_CHECK();
+    BD_TRY(exclusive_scan(o.cnt.p, o.sptr.p, o.nsl, &o.groups, s));
+    const size_t ent = (size_t)o.groups * 32;
+    BD_TRY(ensure(o.col, ent));
+    const long long fill_threads = (long long)o.nsl * 32;
+    const int fill_grid = (int)((fill_threads + 255) / 256);
+    if (fp32) {
+        o.v.release();
+        BD_TRY(ensure(o.v32, 4 * ent));
+        k_slice_fill<float><<<fill_grid, 256, 0, s>>>(o.nsl, K, M.rp.p, M.ci.p, M.v.p, o.order.p, o.sptr.p,
+                                                     o.col.p, o.v32.p, ent);
+    } else {
+        o.v32.release();
+        BD_TRY(ensure(o.v, 4 * ent));
+        k_slice_fill<double><<<fill_grid, 256, 0, s>>>(o.nsl, K, M.rp.p, M.ci.p, M.v.p, o.order.p, o.sptr.p,
+                                                      o.col.p, o.v.p, ent);
+    }
+    ::bd::note_launch();
+    BD_LAUNCH_CHECK();
+    const int MB = fp32 ? 8 : 4;
+    const long long cap = (long long)kSM * MB * 8;  // one resident wave of 256-thread blocks
+    o.warps = (int)std::min<long long>(cap, ((long long)o.nsl + 7) / 8 * 8);
+    BD_TRY(ensure(o.wsl, (size_t)o.warps + 1));
+    k_slice_warps<<<(o.warps + 256) / 256, 256, 0, s>>>(o.nsl, o.groups, o.warps, o.sptr.p, o.wsl.p);
+    ::bd::note_launch();
+    BD_LAUNCH_CHECK();
+    o.K = K;
+    return BD_OK;
+}
+
+static void drop_sliced(SlicedOp &o)
+{
+    o.K = 0;
+    o.cnt.release();
+    o.col.release();
+    o.v.release();
+    o.v32.release();
+    o.sptr.release();
+    o.wsl.release();
+}
+
+// Operator op (0: A, 1: R, 2: P) of level L in the form its lanes entry names.
+template <class S, class G, class E>
+static int apply_op(const Level &L, int op, const S *csr_vals, G g, E e, cudaStream_t s)
+{
+    const int T = L.lanes[op];
+    if (T < 0) return launch_sliced<S>(L.sl[op], -T, g, e, s);
+    return launch_bsr<S>(op == 0 ? L.A : (op == 1 ? L.R : L.P), csr_vals, T, g, e, s);
+}
+
+// Lanes per block row, from per-operator timings inside the V-cycle on the
+// 128x128x32 slab's levels.  Every lane-level reduction step costs adds,
+// which are scarce in FP64 on this part, so FP64 rows use as few lanes as
+// their length allows; FP32 adds are cheap, so FP32 rows use more lanes to
+// shorten each thread's chain of dependent loads.  Small levels get more lanes
+// so the grid still fills the GPU.  Levels with few, long rows (the dense-ish
+// coarse levels): a warp per row in FP64 (a thread block's extra reduction
+// steps cost more FP64 adds than its extra lanes save), a thread block per
+// row in FP32.
 static int lanes_for(const BSR &A, bool fp32)
 {
-    double avg = A.nbr > 0 ? (double)A.nb / A.nbr : 1.0;
+    const double avg = A.nbr > 0 ? (double)A.nb / A.nbr : 1.0;
     int T;
-    if (fp32) T = avg <= 12 ? 1 : (avg <= 48 ? 4 : (avg <= 160 ? 16 : 32));
+    if (fp32) T = avg <= 3 ? 1 : (avg <= 12 ? 2 : (avg <= 48 ? 4 : (avg <= 100 ? 8 : (avg <= 160 ? 16 : 32))));
     else T = avg <= 40 ? 1 : (avg <= 160 ? 4 : (avg <= 640 ? 8 : 16));
     while (T < 32 && (long long)A.nbr * T < 65536) T <<= 1;
-    if ((long long)A.nbr * 32 < 131072 && avg > 96) {  // few long rows: a block per row
+    if ((long long)A.nbr * 32 < 131072 && avg > 96) {  // few long rows
+        if (!fp32) return A.nbr >= 2048 ? 32 : (avg <= 600 ? 64 : 128);
         T = 64;
         while (T < 256 && T * 3 < avg) T <<= 1;
     }
     return T;
+}
+
+// The sliced form (FP64 only: in FP32 block-CSR with more lanes was as fast
+// or faster on every level) where it beat block-CSR inside the V-cycle: many
+// short, ragged rows (the finest prolongator: sorted rows leave few idle
+// lanes, one lane per row needs no reduction) and many long rows (the finest
+// restriction, 8 lanes per row).  Elsewhere the block-CSR rule.
+constexpr int kSlicedMinRows = 8192;
+static int lanes_rule(const BSR &A, bool fp32, bool sliced_ok)
+{
+    const double avg = A.nbr > 0 ? (double)A.nb / A.nbr : 1.0;
+    if (sliced_ok && !fp32 && A.nbr >= kSlicedMinRows) {
+        if (A.nbr >= 65536 && avg <= 16.0) return -1;
+        if (avg >= 96.0) return -8;
+    }
+    return lanes_for(A, fp32);
 }
 
 __global__ void k_sell_width(int N, const int *__restrict__ rp, int *__restrict__ w, int nslices)
@@ -489,7 +751,7 @@ static int apply_level(amg_hierarchy *h, int l, const LV<S> &lv, G g, E e, cudaS
         return BD_OK;
     }
     if constexpr (SU) return BD_EINVAL;
-    else return launch_bsr<S>(L.A, lv.Av, L.lanes[0], g, e, s);
+    else return apply_op<S>(L, 0, lv.Av, g, e, s);
 }
 
 // ------------------------------------------------------------------ live kernel timing
@@ -720,7 +982,7 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
         const Level &C = h->lev[l + 1];
         const LV<S> cv = view<S>(h, l + 1);
         int sx = prof_begin(h, s, 16 * l + R_RESTRICT, false);
-        BD_TRY(launch_bsr<S>(L.R, lv.Rv, L.lanes[1], GatherVec<S>{lv.r},
+        BD_TRY(apply_op<S>(L, 1, lv.Rv, GatherVec<S>{lv.r},
                              EpiStoreD0<S>{cv.f, cv.d, cv.invd, (S)C.ch_inv_theta}, s));
         prof_end(h, sx, 0.0, 0.0, s);
         return BD_OK;
@@ -733,7 +995,7 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
         v2<S> *u = l == 0 ? u0 : lv.u;
         const LV<S> cv = view<S>(h, l + 1);
         int sp = prof_begin(h, s, 16 * l + R_PROLONG, false);
-        BD_TRY(launch_bsr<S>(L.P, lv.Pv, L.lanes[2], GatherVec<S>{cv.u},
+        BD_TRY(apply_op<S>(L, 2, lv.Pv, GatherVec<S>{cv.u},
                              EpiAdd<S, SU>{u}, s));
         prof_end(h, sp, 0.0, 0.0, s);
         int s1 = prof_begin(h, s, 16 * l + R_POST1, l == 0);
@@ -1208,45 +1470,55 @@ static void xr_update(const amg_hierarchy *h, int N, double2 *x, double2 *r, con
 }
 
 // ------------------------------------------------------------------ lane autotuning
-// Candidates: powers of two from (average blocks per row)/16 lanes per row
-// to 4x the average, 64/128/256 meaning a thread block per row (rows of 32
-// blocks and more only).  Each is timed three times, every launch after L2 has been
-// flushed by writing a buffer larger than it (in the V-cycle every coarse
-// operator runs after the finest level has streamed far more than L2
-// through, so cold timings rank the candidates the way the solve sees them);
-// the median counts.  All launches of one operator are queued with their
-// events and read after a single synchronisation.
-constexpr int kLaneCands = 9, kLaneReps = 3;
-constexpr long long kTuneMinBlocks = 20000;  // smaller operators keep the row-length rule
+// Candidates: block-CSR with powers of two from (average blocks per row)/16
+// lanes per row to 4x the average, 64/128/256 meaning a thread block per row
+// (rows of 32 blocks and more only), and, where the operator may take it, the
+// sliced form with 1, 2, 4 and 8 lanes per row (FP64, operators of 8192 rows
+// and more).  Each runs once untimed, then three times back to back, and the
+// median counts: the V-cycle applies a level's operator several times in a
+// row (smoother, residual), so warm timings rank the candidates the way the
+// solve sees them (timings after an L2 flush ranked the middle level's
+// operator the other way round).  The launches of all block-CSR candidates
+// are queued with their events and read after one synchronisation; each
+// sliced candidate is built, timed and synchronised in turn (the next one
+// reuses its buffers).
+constexpr int kLaneCands = 13, kLaneReps = 3;
+constexpr long long kTuneMinBlocks = 20000;  // smaller operators keep the rule
 
 template <class S>
-static int tune_operator(const BSR &M, const S *vals, const v2<S> *x, const v2<S> *f, v2<S> *out,
-                         void *flush, size_t flush_bytes, cudaEvent_t (*ev)[kLaneReps][2], cudaStream_t s,
-                         int *lanes)
+static int tune_operator(Level &L, int op, bool sliced_ok, const v2<S> *x, const v2<S> *f, v2<S> *out,
+                         const S *vals, cudaEvent_t (*ev)[kLaneReps][2], cudaStream_t s)
 {
+    const BSR &M = op == 0 ? L.A : (op == 1 ? L.R : L.P);
+    const bool fp32 = sizeof(S) == 4;
     const double avg = M.nbr > 0 ? (double)M.nb / M.nbr : 1.0;
     const EpiResid<S> epi{f, out};
-    // rows of avg blocks: from avg/16 lanes (16 blocks per lane) up to 4 avg,
-    // a thread block per row only for rows of 32 blocks and more
     int Tlo = 1, Thi = 256;
     while (Tlo * 16 < avg && Tlo < 32) Tlo <<= 1;
     while (Thi > 1 && Thi > 4.0 * avg) Thi >>= 1;
     if (avg < 32.0) Thi = std::min(Thi, 32);
     Thi = std::max(Thi, Tlo);
     int cand[kLaneCands], nc = 0;
-    for (int T = Tlo; T <= Thi && nc < kLaneCands; T <<= 1) cand[nc++] = T;
-    for (int c = 0; c < nc; c++)
+    for (int T = Tlo; T <= Thi && nc < kLaneCands - 4; T <<= 1) cand[nc++] = T;
+    const int ncsr = nc;
+    if (sliced_ok && !fp32 && M.nbr >= kSlicedMinRows)
+        for (int K = 1; K <= 8; K <<= 1) cand[nc++] = -K;
+    const int rule = L.lanes[op];
+    for (int c = 0; c < nc; c++) {
+        if (cand[c] < 0) BD_TRY(build_sliced(M, -cand[c], fp32, L.sl[op], s));
+        L.lanes[op] = cand[c];
+        BD_TRY(apply_op<S>(L, op, vals, GatherVec<S>{x}, epi, s));
         for (int k = 0; k < kLaneReps; k++) {
-            BD_CUDA(cudaMemsetAsync(flush, k, flush_bytes, s));
             BD_CUDA(cudaEventRecord(ev[c][k][0], s));
-            BD_TRY(launch_bsr<S>(M, vals, cand[c], GatherVec<S>{x}, epi, s));
+            BD_TRY(apply_op<S>(L, op, vals, GatherVec<S>{x}, epi, s));
             BD_CUDA(cudaEventRecord(ev[c][k][1], s));
         }
+        if (cand[c] < 0 || c + 1 == ncsr) BD_CUDA(cudaStreamSynchronize(s));
+    }
     BD_CUDA(cudaStreamSynchronize(s));
-    // the fastest median wins unless the row-length rule's count (*lanes on
-    // entry, when among the candidates) is within 3 % of it: near-ties then
-    // resolve the same way on every run
-    const int rule = *lanes;
+    // the fastest median wins unless the rule's choice (when among the
+    // candidates) is within 3 % of it: near-ties then resolve the same way
+    // on every run
     float best = 0.0f, t_rule = -1.0f;
     int bestT = rule;
     for (int c = 0; c < nc; c++) {
@@ -1259,24 +1531,21 @@ static int tune_operator(const BSR &M, const S *vals, const v2<S> *x, const v2<S
             bestT = cand[c];
         }
     }
-    *lanes = (t_rule >= 0.0f && t_rule <= 1.03f * best) ? rule : bestT;
+    const int pick = (t_rule >= 0.0f && t_rule <= 1.03f * best) ? rule : bestT;
+    L.lanes[op] = pick;
+    if (pick > 0) drop_sliced(L.sl[op]);
+    else if (L.sl[op].K != -pick) BD_TRY(build_sliced(M, -pick, fp32, L.sl[op], s));
     return BD_OK;
 }
 
-// Time the candidate lane counts of every block-CSR operator the V-cycle
-// applies (A where the finest level is not sliced ELL, R and P) on this GPU
-// and keep the fastest.  The workspace vectors serve as operands; their
-// contents do not matter.  Lanes change the order of a row's sum, so the
-// choice is fixed per hierarchy: every solve with it is reproducible.
+// Time the candidate forms of every block operator the V-cycle applies (A
+// below the finest level, or on it where it is not sliced ELL; R and P) on
+// this GPU and keep the fastest.  The workspace vectors serve as operands;
+// their contents do not matter.  The form changes the order of a row's sum,
+// so the choice is fixed per hierarchy: every solve with it is reproducible.
 template <class S>
 static int autotune_lanes(amg_hierarchy *h, cudaStream_t s)
 {
-    const size_t flush_bytes = (size_t)192 << 20;  // > the 126 MB L2
-    DBuf<unsigned char> flush;
-    if (flush.alloc(flush_bytes) != BD_OK) {  // no room to time: the row-length rule stays
-        cudaGetLastError();
-        return BD_OK;
-    }
     cudaEvent_t ev[kLaneCands][kLaneReps][2] = {};
     int st = BD_OK;
     for (auto &c : ev)
@@ -1294,7 +1563,7 @@ static int autotune_lanes(amg_hierarchy *h, cudaStream_t s)
             const v2<S> *x = op == 0 ? lv.u : (op == 1 ? lv.r : cv.u);
             const v2<S> *f = op == 1 ? cv.f : lv.f;
             v2<S> *out = op == 0 ? lv.r : (op == 1 ? cv.r : lv.w);
-            st = tune_operator<S>(M, vals, x, f, out, flush.p, flush_bytes, ev, s, &L.lanes[op]);
+            st = tune_operator<S>(L, op, op > 0 || l > 0, x, f, out, vals, ev, s);
         }
     }
     for (auto &c : ev)
@@ -1373,11 +1642,20 @@ int prepare_solve(amg_hierarchy *h, cudaStream_t s)
     if (!h->host_scal) BD_CUDA(cudaMallocHost((void **)&h->host_scal, sizeof(double) * S_NSLOTS));
     if (!h->host_init) BD_CUDA(cudaMallocHost((void **)&h->host_init, sizeof(double) * S_NSLOTS));
     // lanes per block row of the V-cycle's block-CSR operators
+    // (the sliced form for A only below the finest level: the PCG's fused
+    // A p and residual reductions on a non-sliced-ELL finest level use
+    // block-CSR; nothing on the coarsest level, which is solved densely)
     for (int l = 0; l < h->nlev; l++) {
         Level &L = h->lev[l];
-        L.lanes[0] = lanes_for(L.A, p32);
-        L.lanes[1] = l < h->nlev - 1 ? lanes_for(L.R, p32) : 0;
-        L.lanes[2] = l < h->nlev - 1 ? lanes_for(L.P, p32) : 0;
+        const bool last = l == h->nlev - 1;
+        L.lanes[0] = lanes_rule(L.A, p32, l > 0 && !last);
+        L.lanes[1] = last ? 0 : lanes_rule(L.R, p32, true);
+        L.lanes[2] = last ? 0 : lanes_rule(L.P, p32, true);
+        for (int op = 0; op < 3; op++) {
+            if (L.lanes[op] < 0)
+                BD_TRY(build_sliced(op == 0 ? L.A : (op == 1 ? L.R : L.P), -L.lanes[op], p32, L.sl[op], s));
+            else drop_sliced(L.sl[op]);
+        }
     }
     if (h->opts.autotune) BD_TRY(p32 ? autotune_lanes<float>(h, s) : autotune_lanes<double>(h, s));
     BD_CUDA(cudaStreamSynchronize(s));
@@ -1816,6 +2094,7 @@ extern "C" int amg_batch_create(amg_hierarchy *const *h, int count, amg_batch **
         delete b;
         return st;
     }
+    for (amg_hierarchy *hk : g.h) hk->batch_refs++;
     *out = b;
     return BD_OK;
 }
@@ -1872,7 +2151,44 @@ extern "C" int amg_batch_solve(amg_batch *b, const double *const *f, double *con
     return worst;
 }
 
-extern "C" void amg_batch_destroy(amg_batch *b) { delete b; }
+extern "C" void amg_batch_destroy(amg_batch *b)
+{
+    if (!b) return;
+    for (amg_hierarchy *hk : b->g.h) hk->batch_refs--;
+    delete b;
+}
+
+extern "C" int amg_set_level_lanes(amg_hierarchy *h, int level, const int lanes[3], void *stream)
+{
+    if (!h || !lanes || level < 0 || level >= h->nlev) return BD_EINVAL;
+    if (h->batch_refs > 0) return BD_ESTATE;
+    Level &L = h->lev[level];
+    const bool last = level == h->nlev - 1;
+    for (int op = 0; op < 3; op++) {
+        const int T = lanes[op];
+        if (T == 0) continue;
+        const bool applied = !last && !(op == 0 && level == 0 && h->sell.valid);
+        const bool csr_ok = T > 0 && T <= 256 && (T & (T - 1)) == 0;
+        const bool sliced_ok = T < 0 && sliced_k_ok(-T) && !(op == 0 && level == 0);
+        if (!applied || !(csr_ok || sliced_ok)) return BD_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    BD_CUDA(cudaStreamSynchronize(s));
+    for (int op = 0; op < 3; op++) {
+        const int T = lanes[op];
+        if (T == 0) continue;
+        if (T < 0) BD_TRY(build_sliced(op == 0 ? L.A : (op == 1 ? L.R : L.P), -T, h->prec32, L.sl[op], s));
+        else drop_sliced(L.sl[op]);
+        L.lanes[op] = T;
+    }
+    // the captured whole-solve graph holds the old launches: capture anew
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->graph_exec = nullptr;
+    h->graph = nullptr;
+    h->graph_failed = false;
+    return BD_OK;
+}
 
 extern "C" int amg_vcycle(amg_hierarchy *h, const double *r, double *z, int on_device, void *stream)
 {

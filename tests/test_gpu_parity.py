@@ -246,8 +246,8 @@ def test_graph_solve_equals_host_loop_solve(B, precision):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_autotuned_lanes_solve(B, oracle_lib, precision):
-    """amg_options.autotune times the lane counts on the GPU: every chosen
-    count is a valid kernel shape, the V-cycle stays within the V-cycle bound
+    """amg_options.autotune times the operator forms on the GPU: every chosen
+    form is a valid kernel shape, the V-cycle stays within the V-cycle bound
     of the oracle (FP64), the solve still meets the oracle's solution, and the
     graph and loop forms agree bit for bit with the tuned choice."""
     m = MESHES[3]
@@ -260,9 +260,10 @@ def test_autotuned_lanes_solve(B, oracle_lib, precision):
         if l == nl - 1:
             assert lanes == (0, 0, 0)
             continue
-        assert lanes[0] == 0 if l == 0 else lanes[0] in (1, 2, 4, 8, 16, 32, 64, 128, 256)
-        assert lanes[1] in (1, 2, 4, 8, 16, 32, 64, 128, 256)
-        assert lanes[2] in (1, 2, 4, 8, 16, 32, 64, 128, 256)
+        forms = (1, 2, 4, 8, 16, 32, 64, 128, 256, -1, -2, -4, -8)  # -K: sliced
+        assert lanes[0] == 0 if l == 0 else lanes[0] in forms
+        assert lanes[1] in forms
+        assert lanes[2] in forms
     o = oracle_lib.assemble(m, W.DEFAULT_PARAMS, fib)
     H = oracle_lib.Hierarchy(o["A"])
     f = W.rhs(o["A"].shape[0], seed=7)
