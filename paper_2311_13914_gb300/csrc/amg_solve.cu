@@ -301,6 +301,30 @@ __device__ __forceinline__ void stage_stencil(const Stencil &st, int *off)
 // then y_v = c M_p v_p + a, y_u = a + b.  SU: the gathered vector is stored as
 // (v + u, u), which saves the add per node pair (two FP64 operations instead
 // of three where the FP64 pipe is the limit).
+template <class S, class G, bool SU, int UNROLL>
+__device__ __forceinline__ void sell_row(int p, int lane, const int *__restrict__ sptr,
+                                         const int *__restrict__ col, const unsigned char *__restrict__ code,
+                                         const int *off, const v2<S> *__restrict__ kk,
+                                         const S *__restrict__ cm, const G &gather, S &y0, S &y1)
+{
+    constexpr bool CODED = sizeof(S) == 4;
+    const int sl = p >> 5;
+    const int j1 = sptr[sl + 1];
+    S a = 0, b = 0;
+#pragma unroll (UNROLL)
+    for (int j = sptr[sl]; j < j1; j++) {
+        const size_t idx = (size_t)j * 32 + lane;
+        const int q = CODED ? p + off[code[idx]] : col[idx];
+        const v2<S> k = kk[idx];
+        const v2<S> x = gather(q);
+        a = fma(k.x, SU ? x.x : x.x + x.y, a);
+        b = fma(k.y, x.y, b);
+    }
+    const v2<S> xp = gather(p);
+    y0 = fma(cm[p], SU ? xp.x - xp.y : xp.x, a);
+    y1 = a + b;
+}
+
 template <class S, class G, class E, bool SU = false, int MINB = 8>
 __global__ void __launch_bounds__(256, MINB) k_sell(int N, const int *__restrict__ sptr,
                                                const int *__restrict__ col,
@@ -308,25 +332,13 @@ __global__ void __launch_bounds__(256, MINB) k_sell(int N, const int *__restrict
                                                const v2<S> *__restrict__ kk,
                                                const S *__restrict__ cm, G gather, E epi)
 {
-    constexpr bool CODED = sizeof(S) == 4;
     __shared__ int off[27];
-    if (CODED) stage_stencil(st, off);
+    if (sizeof(S) == 4) stage_stencil(st, off);
     const int lane = threadIdx.x & 31, e = share_hi(N);
     for (int p = share_lo(N) + threadIdx.x; p < e; p += blockDim.x) {
-        const int sl = p >> 5;
-        const int j1 = sptr[sl + 1];
-        S a = 0, b = 0;
-#pragma unroll (MINB >= 8 ? 4 : 8)
-        for (int j = sptr[sl]; j < j1; j++) {
-            const size_t idx = (size_t)j * 32 + lane;
-            const int q = CODED ? p + off[code[idx]] : col[idx];
-            const v2<S> k = kk[idx];
-            const v2<S> x = gather(q);
-            a = fma(k.x, SU ? x.x : x.x + x.y, a);
-            b = fma(k.y, x.y, b);
-        }
-        const v2<S> xp = gather(p);
-        epi(p, fma(cm[p], SU ? xp.x - xp.y : xp.x, a), a + b);
+        S y0, y1;
+        sell_row<S, G, SU, (MINB >= 8 ? 4 : 8)>(p, lane, sptr, col, code, off, kk, cm, gather, y0, y1);
+        epi(p, y0, y1);
     }
 }
 
@@ -419,11 +431,12 @@ template <class S, bool SU = false> struct EpiPost2 {
     const v2<S> *__restrict__ w;
     v2<S> *__restrict__ u;
     S c1, c2;
-    __device__ __forceinline__ void operator()(int p, S y0, S y1) const {
+    __device__ __forceinline__ v2<S> value(int p, S y0, S y1) const {
         const v2<S> rp_ = r[p], dp = from_su<S, SU>(d[p]), id = invd[p], wp = w[p];
         const S r0 = rp_.x - y0, r1 = rp_.y - y1;
-        u[p] = V2<S>::mk(wp.x + (c1 * dp.x + c2 * id.x * r0), wp.y + (c1 * dp.y + c2 * id.y * r1));
+        return V2<S>::mk(wp.x + (c1 * dp.x + c2 * id.x * r0), wp.y + (c1 * dp.y + c2 * id.y * r1));
     }
+    __device__ __forceinline__ void operator()(int p, S y0, S y1) const { u[p] = value(p, y0, y1); }
 };
 
 // ------------------------------------------------------------------ per-level views
@@ -948,13 +961,24 @@ __global__ void k_to_f32(long long n, const double *__restrict__ a, float *__res
         b[i] = (float)a[i];
 }
 
+// The PCG's z statistics computed by the V-cycle's last finest-level kernel
+// (defined with the PCG reductions below).
+struct ZOut;
+static int zo_streams(const ZOut *zo);
+template <class S, bool SU>
+static int launch_sell_z(amg_hierarchy *h, const LV<S> &lv, const EpiPost2<S, SU> &epi, const ZOut &zo,
+                         cudaStream_t s);
+
 // One V-cycle in precision S; f0/u0 are the finest level's right-hand side and
 // output (d0 of the finest level must already be in lev[0]'s d vector).  SU0:
 // the finest level's gathered vectors (d0, the iterate u until the last
 // smoothing step, the post-smoother's d) are kept in (v + u, u) form; the
-// output u0 is in (v, u) form either way.
+// output u0 is in (v, u) form either way.  zo (PCG only): the last
+// post-smoothing step on a sliced-ELL finest level writes the FP64 result to
+// zo->z and sums the z statistics (*zdone set); u0 is then not written.
 template <class S, bool SU0>
-static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_t s)
+static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_t s, const ZOut *zo = nullptr,
+                       bool *zdone = nullptr)
 {
     const int nl = h->nlev;
     const bool deg2 = h->opts.cheb_degree == 2;
@@ -1004,9 +1028,17 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
         prof_end(h, s1, l == 0 ? fine_bytes<S>(h, L, 6) : 0.0, fine_flops(h, L, SU), s);
         if (deg2) {
             int s2 = prof_begin(h, s, 16 * l + R_POST2, l == 0);
-            BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{lv.d},
-                                   EpiPost2<S, SU>{lv.r, lv.d, lv.invd, lv.w, u, (S)L.ch_c1, (S)L.ch_c2}, s));
-            prof_end(h, s2, l == 0 ? fine_bytes<S>(h, L, 5) : 0.0, fine_flops(h, L, SU), s);
+            const EpiPost2<S, SU> epi{lv.r, lv.d, lv.invd, lv.w, u, (S)L.ch_c1, (S)L.ch_c2};
+            double bytes = l == 0 ? fine_bytes<S>(h, L, 5) : 0.0;
+            if (l == 0 && zo && h->sell.valid) {
+                BD_TRY((launch_sell_z<S, SU>(h, lv, epi, *zo, s)));
+                if (zdone) *zdone = true;
+                // u is not stored; z written and the PCG's r (and z_old) read in FP64
+                bytes = fine_bytes<S>(h, L, 4) + 16.0 * L.N * (zo_streams(zo));
+            } else {
+                BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{lv.d}, epi, s));
+            }
+            prof_end(h, s2, bytes, fine_flops(h, L, SU), s);
         } else {
             int s2 = prof_begin(h, s, 16 * l + R_POST2, false);
             k_copy2<S><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, lv.w, u); ::bd::note_launch();
@@ -1038,27 +1070,37 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
 }
 
 // z = B r with FP64 vectors at the boundary, in the hierarchy's precision.
-int vcycle_device(amg_hierarchy *h, const double *r_dev, double *z_dev, cudaStream_t s)
+// d0_ready: the producer of r already wrote the finest level's input (D0Out);
+// zo, zdone: as vcycle_impl (z is written to z_dev either way).
+static int vcycle_run(amg_hierarchy *h, const double *r_dev, double *z_dev, cudaStream_t s, bool d0_ready,
+                      const ZOut *zo, bool *zdone)
 {
     Level &L0 = h->lev[0];
+    if (zdone) *zdone = false;
     if (h->prec32) {
         const LV<float> v0 = view<float>(h, 0);
-        int si = prof_begin(h, s, R_VIN, false);
-        k_in32<<<grid_for(L0.N, 256), 256, 0, s>>>(L0.N, (const double2 *)r_dev, v0.invd,
-                                                   (float)L0.ch_inv_theta, v0.f, v0.d); ::bd::note_launch();
-        BD_LAUNCH_CHECK();
-        prof_end(h, si, 0.0, 0.0, s);
-        BD_TRY((vcycle_impl<float, false>(h, v0.f, v0.u, s)));
-        int so = prof_begin(h, s, R_VOUT, false);
-        k_out64<<<grid_for(L0.N, 256), 256, 0, s>>>(L0.N, v0.u, (double2 *)z_dev); ::bd::note_launch();
-        BD_LAUNCH_CHECK();
-        prof_end(h, so, 0.0, 0.0, s);
+        if (!d0_ready) {
+            int si = prof_begin(h, s, R_VIN, false);
+            k_in32<<<grid_for(L0.N, 256), 256, 0, s>>>(L0.N, (const double2 *)r_dev, v0.invd,
+                                                       (float)L0.ch_inv_theta, v0.f, v0.d); ::bd::note_launch();
+            BD_LAUNCH_CHECK();
+            prof_end(h, si, 0.0, 0.0, s);
+        }
+        bool zd = false;
+        BD_TRY((vcycle_impl<float, false>(h, v0.f, v0.u, s, zo, &zd)));
+        if (!zd) {
+            int so = prof_begin(h, s, R_VOUT, false);
+            k_out64<<<grid_for(L0.N, 256), 256, 0, s>>>(L0.N, v0.u, (double2 *)z_dev); ::bd::note_launch();
+            BD_LAUNCH_CHECK();
+            prof_end(h, so, 0.0, 0.0, s);
+        }
+        if (zdone) *zdone = zd;
         return BD_OK;
     }
     // FP64 sliced ELL: the finest level's gathered vectors in (v + u, u) form
     const LV<double> v0 = view<double>(h, 0);
     const bool su = h->sell.valid;
-    if (h->nlev > 1) {
+    if (h->nlev > 1 && !d0_ready) {
         int si = prof_begin(h, s, R_VIN, false);
         if (su)
             k_scale_d0<double, true><<<grid_for(L0.N, 256), 256, 0, s>>>(L0.N, (const double2 *)r_dev, v0.invd,
@@ -1070,8 +1112,13 @@ int vcycle_device(amg_hierarchy *h, const double *r_dev, double *z_dev, cudaStre
         BD_LAUNCH_CHECK();
         prof_end(h, si, 0.0, 0.0, s);
     }
-    return su ? vcycle_impl<double, true>(h, (const double2 *)r_dev, (double2 *)z_dev, s)
-              : vcycle_impl<double, false>(h, (const double2 *)r_dev, (double2 *)z_dev, s);
+    return su ? vcycle_impl<double, true>(h, (const double2 *)r_dev, (double2 *)z_dev, s, zo, zdone)
+              : vcycle_impl<double, false>(h, (const double2 *)r_dev, (double2 *)z_dev, s, zo, zdone);
+}
+
+int vcycle_device(amg_hierarchy *h, const double *r_dev, double *z_dev, cudaStream_t s)
+{
+    return vcycle_run(h, r_dev, z_dev, s, false, nullptr, nullptr);
 }
 
 // ------------------------------------------------------------------ PCG reductions
@@ -1267,6 +1314,35 @@ __global__ void k_zero_if(int N, double2 *__restrict__ x, const double *__restri
         x[i] = make_double2(0.0, 0.0);
 }
 
+// The next V-cycle's finest-level input, written by the kernel that forms the
+// PCG residual r, so that the V-cycle needs no pass of its own over r.  FP64:
+// d0 = D^{-1} r / theta, in (v + u, u) form for a sliced-ELL finest level
+// (mode 1) or in (v, u) form (mode 2); FP32 V-cycle (mode 3): f = (float) r
+// and d0 = D^{-1} f / theta in FP32.  The same arithmetic as k_scale_d0 and
+// k_in32.
+struct D0Out {
+    int mode = 0;  // 0: nothing to write
+    double2 *d64 = nullptr;
+    const double2 *invd64 = nullptr;
+    double it = 0.0;
+    float2 *f32 = nullptr, *d32 = nullptr;
+    const float2 *invd32 = nullptr;
+    float it32 = 0.0f;
+    __device__ __forceinline__ void operator()(int p, double r0, double r1) const
+    {
+        if (mode == 1 || mode == 2) {
+            const double2 b = invd64[p];
+            const double v = r0 * b.x * it, u = r1 * b.y * it;
+            d64[p] = mode == 1 ? make_double2(v + u, u) : make_double2(v, u);
+        } else if (mode == 3) {
+            const float2 b = invd32[p];
+            const float f0 = (float)r0, f1 = (float)r1;
+            f32[p] = make_float2(f0, f1);
+            d32[p] = make_float2(f0 * b.x * it32, f1 * b.y * it32);
+        }
+    }
+};
+
 // FP64 finest-level operator with a reduction epilogue (block CSR form, T lanes).
 // MODE 0: out = A x, partial x.(A x).  MODE 1: out = f - A x (if out), partials
 // ||f - A x||^2 and sum of x_u.  x is in (v, u) form.
@@ -1276,7 +1352,7 @@ __global__ void __launch_bounds__(256) k_bsr_reduce(int N, const int *__restrict
                                                      const double *__restrict__ v,
                                                      const double2 *__restrict__ x,
                                                      const double2 *__restrict__ f,
-                                                     double2 *__restrict__ out, Fin fin)
+                                                     double2 *__restrict__ out, Fin fin, D0Out d0)
 {
     const int lane = threadIdx.x & (T - 1);
     const int groups = (gridDim.x * blockDim.x) / T;
@@ -1309,6 +1385,7 @@ __global__ void __launch_bounds__(256) k_bsr_reduce(int N, const int *__restrict
                 const double2 fp = f[p];
                 const double r0 = fp.x - y0, r1 = fp.y - y1;
                 if (out) out[p] = make_double2(r0, r1);
+                d0(p, r0, r1);
                 acc += r0 * r0 + r1 * r1;
                 xs += xp.y;
             }
@@ -1326,7 +1403,7 @@ __global__ void __launch_bounds__(256, 4) k_sell_reduce(int N, const int *__rest
                                                       const double *__restrict__ cm,
                                                       const double2 *__restrict__ x,
                                                       const double2 *__restrict__ f,
-                                                      double2 *__restrict__ out, Fin fin)
+                                                      double2 *__restrict__ out, Fin fin, D0Out d0)
 {
     double acc = 0.0, xs = 0.0;
     const int lane = threadIdx.x & 31, e = share_hi(N);
@@ -1353,6 +1430,7 @@ __global__ void __launch_bounds__(256, 4) k_sell_reduce(int N, const int *__rest
             const double2 fp = f[p];
             const double r0 = fp.x - y0, r1 = fp.y - y1;
             if (out) out[p] = make_double2(r0, r1);
+            d0(p, r0, r1);
             acc += r0 * r0 + r1 * r1;
             xs += up;
         }
@@ -1364,23 +1442,23 @@ __global__ void __launch_bounds__(256, 4) k_sell_reduce(int N, const int *__rest
 // level is sliced ELL); MODE 1 forms f - A x for an iterate in (v, u) form.
 template <int MODE>
 static void fine_reduce(const amg_hierarchy *h, const double2 *x, const double2 *f, double2 *out,
-                        const Fin &fin, cudaStream_t s)
+                        const Fin &fin, cudaStream_t s, const D0Out &d0 = D0Out{})
 {
     const Level &L0 = h->lev[0];
     if (h->sell.valid) {
         const FineSell &F = h->sell;
         k_sell_reduce<MODE, MODE == 0><<<kSM * 4, 256, 0, s>>>(L0.N, F.sptr.p, F.col.p, (const double2 *)F.kk.p,
-                                                                  F.cm.p, x, f, out, fin); ::bd::note_launch();
+                                                                  F.cm.p, x, f, out, fin, d0); ::bd::note_launch();
         return;
     }
     const BSR &A = L0.A;
     switch (std::min(lanes_for(A, false), 32)) {
-    case 1: k_bsr_reduce<1, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, fin); ::bd::note_launch(); break;
-    case 2: k_bsr_reduce<2, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, fin); ::bd::note_launch(); break;
-    case 4: k_bsr_reduce<4, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, fin); ::bd::note_launch(); break;
-    case 8: k_bsr_reduce<8, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, fin); ::bd::note_launch(); break;
-    case 16: k_bsr_reduce<16, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, fin); ::bd::note_launch(); break;
-    default: k_bsr_reduce<32, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, fin); ::bd::note_launch(); break;
+    case 1: k_bsr_reduce<1, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, fin, d0); ::bd::note_launch(); break;
+    case 2: k_bsr_reduce<2, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, fin, d0); ::bd::note_launch(); break;
+    case 4: k_bsr_reduce<4, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, fin, d0); ::bd::note_launch(); break;
+    case 8: k_bsr_reduce<8, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, fin, d0); ::bd::note_launch(); break;
+    case 16: k_bsr_reduce<16, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, fin, d0); ::bd::note_launch(); break;
+    default: k_bsr_reduce<32, MODE><<<kRedBlocks, 256, 0, s>>>(A.nbr, A.rp.p, A.ci.p, A.v.p, x, f, out, fin, d0); ::bd::note_launch(); break;
     }
 }
 
@@ -1400,6 +1478,65 @@ __global__ void k_z_stats(int N, const double2 *__restrict__ z, const double2 *_
         }
     }
     block_finish<4>(a, b, c, d, fin);
+}
+
+// The V-cycle's last finest-level kernel with the z statistics fused in: the
+// post-smoothed iterate is the preconditioned residual z, stored in FP64, and
+// the sums k_z_stats forms (z_u, r_u, r.z, r.z_old) are taken in FP64 in the
+// same pass (stage 3).
+struct ZOut {
+    double2 *z;
+    const double2 *r;
+    const double2 *zold;  // flexible CG's previous projected z, or null
+    Fin fin;
+};
+
+// FP64: at most 64 registers (4 blocks per SM, as the other FP64 finest-level
+// kernels); FP32: the FP64 sums need more than the 32 registers of 8 blocks
+// per SM, so 6.
+template <class S, bool SU, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_sell_z(int N, const int *__restrict__ sptr,
+                                                    const int *__restrict__ col,
+                                                    const unsigned char *__restrict__ code, Stencil st,
+                                                    const v2<S> *__restrict__ kk, const S *__restrict__ cm,
+                                                    GatherVec<S> gather, EpiPost2<S, SU> epi, ZOut zo)
+{
+    __shared__ int off[27];
+    if (sizeof(S) == 4) stage_stencil(st, off);
+    double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+    const int lane = threadIdx.x & 31, e = share_hi(N);
+    for (int p = share_lo(N) + threadIdx.x; p < e; p += blockDim.x) {
+        S y0, y1;
+        sell_row<S, GatherVec<S>, SU, 4>(p, lane, sptr, col, code, off, kk, cm, gather, y0, y1);
+        const v2<S> u = epi.value(p, y0, y1);
+        const double2 z = make_double2((double)u.x, (double)u.y), r = zo.r[p];
+        zo.z[p] = z;
+        a += z.y;
+        b += r.y;
+        c += r.x * z.x + r.y * z.y;
+        if (zo.zold) {
+            const double2 o = zo.zold[p];
+            d += r.x * o.x + r.y * o.y;
+        }
+    }
+    block_finish<4>(a, b, c, d, zo.fin);
+}
+
+static int zo_streams(const ZOut *zo) { return zo->zold ? 3 : 2; }
+
+template <class S, bool SU>
+static int launch_sell_z(amg_hierarchy *h, const LV<S> &lv, const EpiPost2<S, SU> &epi, const ZOut &zo,
+                         cudaStream_t s)
+{
+    const FineSell &F = h->sell;
+    const int N = h->lev[0].N;
+    constexpr int MB = sizeof(S) == 8 ? 4 : 6;
+    const int grid = (int)std::min<long long>(((long long)N + 31) / 32, (long long)kSM * MB);
+    k_sell_z<S, SU, MB><<<grid, 256, 0, s>>>(N, F.sptr.p, F.col.p, F.code.p, stencil_of(F), lv.kk, lv.cm,
+                                             GatherVec<S>{lv.d}, epi, zo);
+    ::bd::note_launch();
+    BD_LAUNCH_CHECK();
+    return BD_OK;
 }
 
 // z <- z - mean(z_u) e_u; p = z (first iteration) or z + beta p, stored in
@@ -1428,7 +1565,7 @@ __global__ void k_p_update(int N, double2 *__restrict__ z, double2 *__restrict__
 
 template <bool SU>
 __global__ void k_xr_update(int N, double2 *__restrict__ x, double2 *__restrict__ r,
-                            const double2 *__restrict__ p, const double2 *__restrict__ q, Fin fin)
+                            const double2 *__restrict__ p, const double2 *__restrict__ q, Fin fin, D0Out d0)
 {
     const double alpha = fin.scal[S_ALPHA];
     double acc = 0.0;
@@ -1442,6 +1579,7 @@ __global__ void k_xr_update(int N, double2 *__restrict__ x, double2 *__restrict_
         ri.y -= alpha * qi.y;
         x[i] = xi;
         r[i] = ri;
+        d0(i, ri.x, ri.y);
         acc += ri.x * ri.x + ri.y * ri.y;
     }
     block_finish<1>(acc, 0.0, 0.0, 0.0, fin);
@@ -1462,11 +1600,32 @@ static void p_update(const amg_hierarchy *h, int N, double2 *z, double2 *p, doub
 }
 
 static void xr_update(const amg_hierarchy *h, int N, double2 *x, double2 *r, const double2 *p,
-                      const double2 *q, const Fin &fin, cudaStream_t s)
+                      const double2 *q, const Fin &fin, cudaStream_t s, const D0Out &d0)
 {
-    if (h->sell.valid) k_xr_update<true><<<kVecBlocks, kVecThreads, 0, s>>>(N, x, r, p, q, fin);
-    else k_xr_update<false><<<kVecBlocks, kVecThreads, 0, s>>>(N, x, r, p, q, fin);
+    if (h->sell.valid) k_xr_update<true><<<kVecBlocks, kVecThreads, 0, s>>>(N, x, r, p, q, fin, d0);
+    else k_xr_update<false><<<kVecBlocks, kVecThreads, 0, s>>>(N, x, r, p, q, fin, d0);
     note_launch();
+}
+
+// What the producer of the PCG residual writes for the next V-cycle (see
+// D0Out); mode 0 where the V-cycle has no smoothing level and is FP64.
+static D0Out d0_out(amg_hierarchy *h)
+{
+    D0Out d;
+    Level &L0 = h->lev[0];
+    if (h->prec32) {
+        d.mode = 3;
+        d.f32 = (float2 *)L0.f32.p;
+        d.d32 = (float2 *)L0.d32.p;
+        d.invd32 = (const float2 *)L0.invdiag32.p;
+        d.it32 = (float)L0.ch_inv_theta;
+    } else if (h->nlev > 1) {
+        d.mode = h->sell.valid ? 1 : 2;
+        d.d64 = (double2 *)L0.d.p;
+        d.invd64 = (const double2 *)L0.invdiag.p;
+        d.it = L0.ch_inv_theta;
+    }
+    return d;
 }
 
 // ------------------------------------------------------------------ lane autotuning
@@ -1707,7 +1866,8 @@ static int pcg_solve_loop(amg_hierarchy *h, const double *f_dev, double *x_dev, 
     if (!warm) {
         k_zero2<<<kVecBlocks, kVecThreads, 0, s>>>(N, x); ::bd::note_launch();
     }
-    fine_reduce<1>(h, x, fp, r, make_fin(h, 2, 0), s);
+    const D0Out d0 = d0_out(h);
+    fine_reduce<1>(h, x, fp, r, make_fin(h, 2, 0), s, d0);
     BD_LAUNCH_CHECK();
     BD_TRY(read_scal(h, s));
     double ff = h->host_scal[S_FF], sumfu = h->host_scal[S_SUMFU];
@@ -1725,10 +1885,14 @@ static int pcg_solve_loop(amg_hierarchy *h, const double *f_dev, double *x_dev, 
     } else if (status == BD_OK && !(rr <= o->rtol * nf)) {
         status = BD_ENOTCONV;
         while (it < o->max_it) {
-            BD_TRY(vcycle_device(h, (const double *)r, (double *)z, s));
-            int sz = prof_begin(h, s, R_ZSTATS, false);
-            k_z_stats<<<kVecBlocks, kVecThreads, 0, s>>>(N, z, r, it == 0 ? nullptr : zold, make_fin(h, 3, it == 0)); ::bd::note_launch();
-            prof_end(h, sz, 0.0, 0.0, s);
+            const ZOut zo{z, r, it == 0 ? nullptr : zold, make_fin(h, 3, it == 0)};
+            bool zd = false;
+            BD_TRY(vcycle_run(h, (const double *)r, (double *)z, s, true, &zo, &zd));
+            if (!zd) {
+                int sz = prof_begin(h, s, R_ZSTATS, false);
+                k_z_stats<<<kVecBlocks, kVecThreads, 0, s>>>(N, z, r, zo.zold, zo.fin); ::bd::note_launch();
+                prof_end(h, sz, 0.0, 0.0, s);
+            }
             int su = prof_begin(h, s, R_PUPDATE, false);
             p_update(h, N, z, p, zold, scal, it == 0, s);
             prof_end(h, su, 0.0, 0.0, s);
@@ -1738,7 +1902,7 @@ static int pcg_solve_loop(amg_hierarchy *h, const double *f_dev, double *x_dev, 
             fine_reduce<0>(h, p, nullptr, q, make_fin(h, 4, 0), s);
             prof_end(h, sq, h->prec32 ? 0.0 : fine_bytes<double>(h, L0, 2), fine_flops(h, L0, true), s);
             int sx = prof_begin(h, s, R_XRUPDATE, false);
-            xr_update(h, N, x, r, p, q, make_fin(h, 2, 0), s);
+            xr_update(h, N, x, r, p, q, make_fin(h, 2, 0), s, d0);
             prof_end(h, sx, 0.0, 0.0, s);
             BD_LAUNCH_CHECK();
             BD_TRY(read_scal(h, s));
@@ -1825,7 +1989,8 @@ static int capture_solve(amg_hierarchy *h, cudaStream_t s, cudaStream_t s2)
     BD_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
     cudaGraphConditionalHandle cond;
     BD_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 0, 0));
-    fine_reduce<1>(h, x, fp, r, make_fin(h, 6, 0, cond), s);
+    const D0Out d0 = d0_out(h);
+    fine_reduce<1>(h, x, fp, r, make_fin(h, 6, 0, cond), s, d0);
     BD_LAUNCH_CHECK();
     BD_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
     cudaGraphNodeParams np = {};
@@ -1838,11 +2003,15 @@ static int capture_solve(amg_hierarchy *h, cudaStream_t s, cudaStream_t s2)
     cudaGraph_t body = np.conditional.phGraph_out[0];
     const long long c1 = launch_count();
     BD_CUDA(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    BD_TRY(vcycle_device(h, (const double *)r, (double *)z, s2));
-    k_z_stats<<<kVecBlocks, kVecThreads, 0, s2>>>(N, z, r, zold, make_fin(h, 3, -1)); ::bd::note_launch();
+    const ZOut zo{z, r, zold, make_fin(h, 3, -1)};
+    bool zd = false;
+    BD_TRY(vcycle_run(h, (const double *)r, (double *)z, s2, true, &zo, &zd));
+    if (!zd) {
+        k_z_stats<<<kVecBlocks, kVecThreads, 0, s2>>>(N, z, r, zold, zo.fin); ::bd::note_launch();
+    }
     p_update(h, N, z, p, zold, scal, -1, s2);
     fine_reduce<0>(h, p, nullptr, q, make_fin(h, 4, 0), s2);
-    xr_update(h, N, x, r, p, q, make_fin(h, 7, 0, cond), s2);
+    xr_update(h, N, x, r, p, q, make_fin(h, 7, 0, cond), s2, d0);
     BD_LAUNCH_CHECK();
     cudaGraph_t body_out = nullptr;
     BD_CUDA(cudaStreamEndCapture(s2, &body_out));

@@ -308,8 +308,8 @@ def test_large_coarsest_level_matches_oracle(B, oracle_lib, m, limit):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_profile_breakdown_covers_the_solve(B, precision):
     """Profiling level 2 times every solve-phase step: all V-cycle steps of
-    every level appear once per iteration, the PCG steps once per iteration,
-    and level 1 keeps its finest-operator sums."""
+    every level appear once per iteration, the PCG steps once per iteration
+    (the fused ones not at all), and level 1 keeps its finest-operator sums."""
     m = MESHES[0]
     sysh = B.bd_assemble(m, W.DEFAULT_PARAMS, W.fibre_table(m))
     h = B.amg_setup(sysh, B.amg_options_default(precision=precision))
@@ -323,8 +323,12 @@ def test_profile_breakdown_covers_the_solve(B, precision):
     for l in range(nl - 1):
         for role in B.PROFILE_ROLES:
             assert bd[f"L{l}_{role}"][1] == it
-    for step in ("coarse", "z_stats", "p_update", "A_p", "x_r_update"):
+    for step in ("coarse", "p_update", "A_p", "x_r_update"):
         assert bd[step][1] == it
+    # the z statistics ride on the last finest-level smoothing kernel and the
+    # V-cycle's input on the residual update: neither is a step of its own
+    for step in ("z_stats", "vcycle_in", "vcycle_out"):
+        assert step not in bd
     assert all(ms > 0.0 for ms, _ in bd.values())
     prof = B.amg_profile_read(h)
     assert prof["launches"] == it * (4 if precision else 5)
