@@ -1221,8 +1221,8 @@ __device__ void finish_stage(const Fin &f, double a, double b, double c, double 
 // l, l + 32, ... in index order) and folds its 32 lane sums by shuffles into
 // tot[k].  That is 12 FP64 warp additions per value and block for 256 threads,
 // where a shuffle tree in every warp costs 45.
-template <int NV>
-__device__ __forceinline__ void block_sum(const double (&v)[4], double (*buf)[kMaxBlockThreads], double *tot)
+template <int NV, int BT>
+__device__ __forceinline__ void block_sum(const double (&v)[4], double (*buf)[BT], double *tot)
 {
 #pragma unroll
     for (int k = 0; k < NV; k++) buf[k][threadIdx.x] = v[k];
@@ -1241,15 +1241,17 @@ __device__ __forceinline__ void block_sum(const double (&v)[4], double (*buf)[kM
 // partials in a fixed order (independent of which block is last, so the
 // result is reproducible) and applies the stage.  No waiting: blocks that are
 // not last simply exit.  NV of (a, b, c, d) are live; the stage sees zeros for
-// the rest.  Needs blockDim.x <= kMaxBlockThreads and a multiple of 32.
-template <int NV>
+// the rest.  Needs blockDim.x <= BT and a multiple of 32 (the shared buffer
+// holds BT values per sum: kernels of 256 threads keep the rest of shared
+// memory for L1).
+template <int NV, int BT = kMaxBlockThreads>
 __device__ void block_finish(double a, double b, double c, double d, const Fin &f)
 {
-    __shared__ double buf[NV][kMaxBlockThreads];
+    __shared__ double buf[NV][BT];
     __shared__ double tot[4];
     __shared__ bool last;
     double v[4] = {a, b, c, d};
-    block_sum<NV>(v, buf, tot);
+    block_sum<NV, BT>(v, buf, tot);
     if (threadIdx.x == 0) {
         double *o = f.partial + kPart * blockIdx.x;
 #pragma unroll
@@ -1268,7 +1270,7 @@ __device__ void block_finish(double a, double b, double c, double d, const Fin &
 #pragma unroll
         for (int k = 0; k < NV; k++) v[k] += q[k];
     }
-    block_sum<NV>(v, buf, tot);
+    block_sum<NV, BT>(v, buf, tot);
     if (threadIdx.x == 0) {
         finish_stage(f, tot[0], NV > 1 ? tot[1] : 0.0, NV > 2 ? tot[2] : 0.0, NV > 3 ? tot[3] : 0.0);
         *f.counter = 0u;
@@ -1391,7 +1393,7 @@ __global__ void __launch_bounds__(256) k_bsr_reduce(int N, const int *__restrict
             }
         }
     }
-    block_finish<MODE == 0 ? 1 : 2>(acc, xs, 0.0, 0.0, fin);
+    block_finish<MODE == 0 ? 1 : 2, 256>(acc, xs, 0.0, 0.0, fin);
 }
 
 // Same with the sliced-ELL finest level.  SU: x is stored as (v + u, u), so a
@@ -1435,7 +1437,7 @@ __global__ void __launch_bounds__(256, 4) k_sell_reduce(int N, const int *__rest
             xs += up;
         }
     }
-    block_finish<MODE == 0 ? 1 : 2>(acc, xs, 0.0, 0.0, fin);
+    block_finish<MODE == 0 ? 1 : 2, 256>(acc, xs, 0.0, 0.0, fin);
 }
 
 // MODE 0 applies A to the search direction (in (v+u, u) form when the finest
@@ -1507,7 +1509,8 @@ __global__ void __launch_bounds__(256, MINB) k_sell_z(int N, const int *__restri
     const int lane = threadIdx.x & 31, e = share_hi(N);
     for (int p = share_lo(N) + threadIdx.x; p < e; p += blockDim.x) {
         S y0, y1;
-        sell_row<S, GatherVec<S>, SU, 4>(p, lane, sptr, col, code, off, kk, cm, gather, y0, y1);
+        sell_row<S, GatherVec<S>, SU, (sizeof(S) == 8 ? 8 : 4)>(p, lane, sptr, col, code, off, kk, cm, gather, y0,
+                                                                 y1);
         const v2<S> u = epi.value(p, y0, y1);
         const double2 z = make_double2((double)u.x, (double)u.y), r = zo.r[p];
         zo.z[p] = z;
@@ -1519,7 +1522,7 @@ __global__ void __launch_bounds__(256, MINB) k_sell_z(int N, const int *__restri
             d += r.x * o.x + r.y * o.y;
         }
     }
-    block_finish<4>(a, b, c, d, zo.fin);
+    block_finish<4, 256>(a, b, c, d, zo.fin);
 }
 
 static int zo_streams(const ZOut *zo) { return zo->zold ? 3 : 2; }
