@@ -643,16 +643,20 @@ static int lanes_for(const BSR &A, bool fp32)
 
 // The sliced form (FP64 only: in FP32 block-CSR with more lanes was as fast
 // or faster on every level) where it beat block-CSR inside the V-cycle: many
-// short, ragged rows (the finest prolongator: sorted rows leave few idle
-// lanes, one lane per row needs no reduction) and many long rows (the finest
-// restriction, 8 lanes per row).  Elsewhere the block-CSR rule.
+// short, ragged rows (the prolongators of levels of 65536 rows and more:
+// sorted rows leave few idle lanes, one lane per row needs no reduction), many
+// long rows (restrictions, 8 lanes per row) and, on levels of 65536 rows and
+// more, rows in between (4 lanes; the autotuner's choices on the 256x256x64
+// slab's second level, while block-CSR with 4 lanes won on the 31542 rows of
+// the 128x128x32 slab's).  Elsewhere the block-CSR rule.
 constexpr int kSlicedMinRows = 8192;
 static int lanes_rule(const BSR &A, bool fp32, bool sliced_ok)
 {
     const double avg = A.nbr > 0 ? (double)A.nb / A.nbr : 1.0;
     if (sliced_ok && !fp32 && A.nbr >= kSlicedMinRows) {
-        if (A.nbr >= 65536 && avg <= 16.0) return -1;
+        if (A.nbr >= 65536 && avg <= 24.0) return -1;
         if (avg >= 96.0) return -8;
+        if (A.nbr >= 65536) return -4;  // middle-length rows of a big level
     }
     return lanes_for(A, fp32);
 }
@@ -1265,10 +1269,14 @@ __device__ void block_finish(double a, double b, double c, double d, const Fin &
     __threadfence();
 #pragma unroll
     for (int k = 0; k < 4; k++) v[k] = 0.0;
+    // L2 loads (the partials were published by the other blocks' fences and
+    // tickets), not volatile ones, so that the unrolled loads of several
+    // partials are in flight together: the last block's serial tail
+#pragma unroll 4
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-        const volatile double *q = f.partial + kPart * i;
+        const double *q = f.partial + kPart * i;
 #pragma unroll
-        for (int k = 0; k < NV; k++) v[k] += q[k];
+        for (int k = 0; k < NV; k++) v[k] += __ldcg(q + k);
     }
     block_sum<NV, BT>(v, buf, tot);
     if (threadIdx.x == 0) {
