@@ -283,7 +283,9 @@ void amg_batch_destroy(amg_batch *b);
  * and the flops the kernels execute (an FMA counts 2; the sliced-ELL form of
  * the finest level needs 2 FMA per stored node pair with its gathered vector
  * in (v + u, u) form, 2 FMA and an add otherwise, where the 2x2-block operator
- * would take 8 flops per block) are summed.  Switching it on resets the sums, switching it off keeps them
+ * would take 8 flops per block) are summed; the last post-smoothing launch
+ * with the PCG's z statistics counts its FP64 streams (r read, z written, and
+ * z_old read in the flexible form) too.  Switching it on resets the sums, switching it off keeps them
  * for amg_profile_read; reading requires no pending work.  enable: 0 off,
  * 1 on, 2 on with the per-step breakdown below.  While it is on,
  * solves run the host-driven loop (one launch at a time) instead of the
@@ -306,7 +308,11 @@ int amg_profile_read(const amg_hierarchy *h, amg_kernel_profile *out);
  * the post-smoother's two steps) and 240 + k for the rest (k = 0 coarsest
  * solve, 1 V-cycle input, 2 V-cycle output, 3 preconditioned-residual
  * statistics, 4 search-direction update, 5 A p with p.Ap, 6 iterate and
- * residual update).  Steps shorter than the host's launch rate read high.
+ * residual update).  Steps fused into others have no entry of their own: on a
+ * sliced-ELL finest level the statistics ride on the last post-smoothing step
+ * (16 * 0 + 5), and in the PCG the V-cycle input is written by the residual
+ * update (so k = 1, 2, 3 appear only for amg_vcycle or a finest level in
+ * block-CSR form).  Steps shorter than the host's launch rate read high.
  * Switching profiling on from off resets these sums too. */
 int amg_profile_breakdown(const amg_hierarchy *h, double *ms, long long *count);
 
