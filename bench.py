@@ -59,7 +59,8 @@ def parse_args(argv=None):
                          "Default 0 in the time-stepping mode (the rule matched the fastest "
                          "form inside the V-cycle on every operator of the 128x128x32 slab, "
                          "while single-launch timings misranked one, and setup is inside the "
-                         "timed step), 1 in the other modes")
+                         "timed step) except for the large workload, whose levels the rule "
+                         "was not calibrated on; 1 in the other modes")
     ap.add_argument("--no-autotune", dest="autotune", action="store_const", const=0,
                     help="same as --autotune 0")
     ap.add_argument("--coarse-eq-limit", type=int, default=None,
@@ -810,7 +811,9 @@ def main(argv=None):
     if args.mode == "step" and args.coarse_eq_limit is None:
         args.coarse_eq_limit = STEP_COARSE_EQ_LIMIT
     if args.autotune is None:
-        args.autotune = 0 if args.mode == "step" else 1
+        # the rule was calibrated on the 128x128x32 slab's levels; larger slabs
+        # (whose levels it was not calibrated on) and the other modes time the forms
+        args.autotune = 0 if args.mode == "step" and args.workload != "large" else 1
     if args.mode == "serve":
         out = run_serve(args)
     elif args.mode == "batch":
