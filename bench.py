@@ -806,14 +806,19 @@ def run_sweep(args):
 STEP_COARSE_EQ_LIMIT = 2000  # time-stepping mode's coarsest level (see --coarse-eq-limit)
 
 
-def main(argv=None):
-    args = parse_args(argv)
+def resolve_defaults(args):
+    """Mode-dependent defaults of the options left unset on the command line."""
     if args.mode == "step" and args.coarse_eq_limit is None:
         args.coarse_eq_limit = STEP_COARSE_EQ_LIMIT
     if args.autotune is None:
         # the rule was calibrated on the 128x128x32 slab's levels; larger slabs
         # (whose levels it was not calibrated on) and the other modes time the forms
         args.autotune = 0 if args.mode == "step" and args.workload != "large" else 1
+    return args
+
+
+def main(argv=None):
+    args = resolve_defaults(parse_args(argv))
     if args.mode == "serve":
         out = run_serve(args)
     elif args.mode == "batch":
