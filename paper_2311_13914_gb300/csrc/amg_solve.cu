@@ -1645,13 +1645,15 @@ static D0Out d0_out(amg_hierarchy *h)
 // (rows of 32 blocks and more only), and, where the operator may take it, the
 // sliced form with 1, 2, 4 and 8 lanes per row (FP64, operators of 8192 rows
 // and more).  Each runs once untimed, then three times back to back, and the
-// median counts: the V-cycle applies a level's operator several times in a
-// row (smoother, residual), so warm timings rank the candidates the way the
-// solve sees them (timings after an L2 flush ranked the middle level's
-// operator the other way round).  The launches of all block-CSR candidates
-// are queued with their events and read after one synchronisation; each
-// sliced candidate is built, timed and synchronised in turn (the next one
-// reuses its buffers).
+// median counts (the V-cycle applies a level's operator several times in a
+// row: smoother, residual).  Single launches do not rank every operator as the
+// V-cycle does: on the 128x128x32 slab they put the sliced form first for the
+// middle level's A, which inside the V-cycle is 5 % slower than block-CSR with
+// 4 lanes, warm or after an L2 flush; the row-length rule holds the choices
+// measured inside the V-cycle.  The launches of all block-CSR candidates are
+// queued with their events and read after one synchronisation; each sliced
+// candidate is built, timed and synchronised in turn (the next one reuses its
+// buffers).
 constexpr int kLaneCands = 13, kLaneReps = 3;
 constexpr long long kTuneMinBlocks = 20000;  // smaller operators keep the rule
 
