@@ -135,20 +135,23 @@ int bd_dot_exact(const double *x, const double *y, long long n, int on_device, d
                  void *stream);
 
 /* Same result as bd_dot_exact, computed without allocating anything.  The
- * paper has no counterpart: this entry point exists for callers that must not
- * call cudaMalloc -- code running while its stream is being captured into a
- * CUDA graph (an allocation there is an unsupported operation that breaks the
- * capture), latency-critical loops in which an allocation would synchronise
- * the device, and hosts whose device memory belongs to another allocator.
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc -- hosts whose device memory is owned by another allocator
+ * (an application that reserves the GPU's memory for its own pool up front,
+ * leaving none for the library to take), and latency-critical loops in which
+ * an allocation would synchronise the device and stall the pipeline.
  * x, y: n doubles in device memory; out: one double in device memory, written
  * in stream order (the call does not synchronise).  Scratch: one 552-byte
  * accumulator in a static device array that every GPU loading the library
  * holds until exit; each call clears it on `stream` before use.  All calls
  * share that array, so calls whose work overlaps on the GPU (different
  * streams, or concurrent host threads) race and must be serialised by the
- * caller.  The first call on a device looks up the array's device address;
- * make that first call before any stream capture.  Errors: BD_EINVAL (NULL,
- * n < 0), BD_ERANGE (n > 2^31 - 1, the accumulator's carry headroom), BD_ECUDA. */
+ * caller.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make that
+ * first call before any stream capture.  The kept address is not valid after
+ * cudaDeviceReset on that device: do not call this entry point after such a
+ * reset.  Errors: BD_EINVAL (NULL, n < 0), BD_ERANGE (n > 2^31 - 1, the
+ * accumulator's carry headroom), BD_ECUDA. */
 int bd_dot_exact_noalloc(const double *x, const double *y, long long n, double *out, void *stream);
 
 /* ---- a0: Q1 assembly (Section 2.2; Eq. 2; Eq. 3) --------------------------

@@ -8,10 +8,12 @@ shares no code with the CUDA path.  The arithmetic lives in ``bd_oracle.c``
 
 Every function follows a passage of arXiv 2311.13914 (cited in bd_oracle.c).
 Pins that tie it to the paper and to mathematics, not to itself, live in
-``tests/test_oracle_*.py``.  Parity status: assembly, strength, MIS,
-aggregation, prolongators, Galerkin operators, eigen-estimate, smoother,
-coarse solve, V-cycle and PCG are pinned (closed forms, brute force, dense
-linear algebra); the comparison with the paper's own timings is "parity
+``tests/test_oracle_*.py``.  Parity status: assembly (including the fibre
+field sampled at the Gauss z-levels, against an independent quadrature),
+strength, the squared strength graph (against a dense (I + W)^2), MIS,
+aggregation (brute force on the plain and the squared graph), prolongators,
+Galerkin operators, eigen-estimate, smoother, coarse solve, V-cycle and PCG
+are pinned (closed forms, brute force, dense linear algebra); the comparison with the paper's own timings is "parity
 unpinned" because the paper prints no worked example for this system.
 """
 from __future__ import annotations

@@ -299,8 +299,12 @@ def bd_dot_exact(x, y, stream=None) -> float:
 
 
 def bd_dot_exact_noalloc(x, y, out, stream=None):
-    """Allocation-free reproducible dot of two CUDA tensors into the one-element
-    CUDA tensor `out` (stream-ordered, no synchronisation)."""
+    """Allocation-free reproducible dot of two CUDA tensors into the first
+    element of the CUDA tensor `out` (stream-ordered, no synchronisation).
+    stream=None runs on torch's current stream, the one the inputs were most
+    likely written on."""
+    import torch
+
     px, dx, kx = _arr(x, np.float64)
     py, dy, ky = _arr(y, np.float64)
     po, do, ko = _arr(out, np.float64)
@@ -308,6 +312,10 @@ def bd_dot_exact_noalloc(x, y, out, stream=None):
         raise ValueError("x, y and out must be CUDA tensors")
     if kx.numel() != ky.numel():
         raise ValueError("x and y must have the same length")
+    if ko.numel() < 1:
+        raise ValueError("out must hold at least one element")
+    if stream is None:
+        stream = torch.cuda.current_stream()
     _check(lib().bd_dot_exact_noalloc(px, py, kx.numel(), po, _stream(stream)),
            "bd_dot_exact_noalloc")
     return out

@@ -2356,19 +2356,32 @@ extern "C" int amg_set_level_lanes(amg_hierarchy *h, int level, const int lanes[
     }
     cudaStream_t s = (cudaStream_t)stream;
     BD_CUDA(cudaStreamSynchronize(s));
-    for (int op = 0; op < 3; op++) {
-        const int T = lanes[op];
-        if (T == 0) continue;
-        if (T < 0) BD_TRY(build_sliced(op == 0 ? L.A : (op == 1 ? L.R : L.P), -T, h->prec32, L.sl[op], s));
-        else drop_sliced(L.sl[op]);
-        L.lanes[op] = T;
-    }
-    // the captured whole-solve graph holds the old launches: capture anew
+    // The captured whole-solve graph holds the old launches and buffers: drop
+    // it before any buffer changes, so that no error return below leaves a
+    // graph that reads freed or rebuilt memory (the next solve captures anew).
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->graph) cudaGraphDestroy(h->graph);
     h->graph_exec = nullptr;
     h->graph = nullptr;
     h->graph_failed = false;
+    for (int op = 0; op < 3; op++) {
+        const int T = lanes[op];
+        if (T == 0) continue;
+        const BSR &M = op == 0 ? L.A : (op == 1 ? L.R : L.P);
+        if (T < 0) {
+            const int rc = build_sliced(M, -T, h->prec32, L.sl[op], s);
+            if (rc != BD_OK) {
+                // a half-built sliced form is unusable: fall back to the
+                // block-CSR form the rule gives, which needs no extra buffers
+                drop_sliced(L.sl[op]);
+                L.lanes[op] = lanes_for(M, h->prec32);
+                return rc;
+            }
+        } else {
+            drop_sliced(L.sl[op]);
+        }
+        L.lanes[op] = T;
+    }
     return BD_OK;
 }
 

@@ -45,26 +45,30 @@ def time_forms(h, r, candidates=CANDIDATES, reps: int = 5, warm: int = 2, stream
     for level, op in _operators(h):
         start = B.amg_level_lanes(h, level)[op]
         row = {}
-        for form in candidates:
-            if not _valid(level, op, form):
-                continue
-            lanes = [0, 0, 0]
-            lanes[op] = form
-            B.amg_set_level_lanes(h, level, lanes, stream=stream)
-            for _ in range(warm):
-                B.amg_vcycle(h, r, z, stream=stream)
-            B.amg_profile_enable(h, 2)
-            try:
-                for _ in range(reps):
+        try:
+            for form in candidates:
+                if not _valid(level, op, form):
+                    continue
+                lanes = [0, 0, 0]
+                lanes[op] = form
+                B.amg_set_level_lanes(h, level, lanes, stream=stream)
+                for _ in range(warm):
                     B.amg_vcycle(h, r, z, stream=stream)
-                bd = B.amg_profile_breakdown(h)
-            finally:
-                B.amg_profile_enable(h, 0)
-            row[form] = sum(1000.0 * bd[f"L{level}_{role}"][0] / bd[f"L{level}_{role}"][1]
-                            for role in ROLES[op])
-        lanes = [0, 0, 0]
-        lanes[op] = start
-        B.amg_set_level_lanes(h, level, lanes, stream=stream)
+                B.amg_profile_enable(h, 2)
+                try:
+                    for _ in range(reps):
+                        B.amg_vcycle(h, r, z, stream=stream)
+                    bd = B.amg_profile_breakdown(h)
+                finally:
+                    B.amg_profile_enable(h, 0)
+                row[form] = sum(1000.0 * bd[f"L{level}_{role}"][0] / bd[f"L{level}_{role}"][1]
+                                for role in ROLES[op])
+        finally:
+            # the operator goes back to its starting form even when a candidate
+            # failed (e.g. BD_ENOMEM while building a sliced form)
+            lanes = [0, 0, 0]
+            lanes[op] = start
+            B.amg_set_level_lanes(h, level, lanes, stream=stream)
         table[(level, op)] = row
     return table
 

@@ -93,3 +93,21 @@ def test_tune_forms_takes_the_fastest_and_keeps_near_ties(fake):
     for (level, op), form in out["forms"].items():
         assert lib.lanes[level][op] == form
     assert lib.lanes[0][0] == 0                      # the finest A untouched
+
+
+def test_time_forms_restores_the_starting_form_when_a_candidate_fails(fake):
+    lib = fake(lambda level, op, form: 10.0)
+    start = {l: list(v) for l, v in lib.lanes.items()}
+    real_set = lib.amg_set_level_lanes
+
+    def failing_set(h, level, lanes, stream=None):
+        if level == 1 and lanes[0] == -2:
+            # the library's own fallback after a failed sliced build
+            lib.lanes[1][0] = 4
+            raise RuntimeError("amg_set_level_lanes: out of memory")
+        real_set(h, level, lanes, stream)
+    lib.amg_set_level_lanes = failing_set
+    with pytest.raises(RuntimeError):
+        forms.time_forms(None, None, candidates=(1, 8, -2), reps=1, warm=0)
+    assert lib.lanes == start
+    assert lib.sets[-1] == (1, (start[1][0], 0, 0))

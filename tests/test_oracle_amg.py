@@ -137,6 +137,96 @@ def test_aggregation_rule_by_brute_force(oracle_lib):
         assert agg[i] == agg[-mj]
 
 
+# --------------------------------------------------------------- squared graph
+def _dense_square_without_diagonal(S):
+    """(I + W)^2 with its diagonal removed, W the filtered weights (Appendix A,
+    square_graph), computed densely by numpy."""
+    Wd = S.toarray()
+    Wh = np.eye(Wd.shape[0]) + Wd
+    Q = Wh @ Wh
+    np.fill_diagonal(Q, 0.0)
+    return Q
+
+
+def _check_square(oracle_lib, S):
+    S2 = oracle_lib.square_graph(S)
+    Q = _dense_square_without_diagonal(S)
+    got = S2.toarray()
+    # pattern: every pair joined by a path of one or two strong edges, no diagonal
+    assert np.array_equal(got != 0, Q != 0)
+    assert np.all(np.diff(S2.indptr) >= 0) and S2.nnz == np.count_nonzero(Q)
+    # values: 2 w_pq for direct neighbours plus the two-step path weights
+    assert np.allclose(got, Q, rtol=4e-16 * 8, atol=0.0)
+    # symmetric input -> symmetric square
+    assert (S2 != S2.T).nnz == 0 or np.abs((S2 - S2.T).toarray()).max() <= 1e-15 * np.abs(Q).max()
+    for i in range(S2.shape[0]):
+        cols = S2.indices[S2.indptr[i]:S2.indptr[i + 1]]
+        assert np.all(np.diff(cols) > 0) and i not in cols
+    return S2
+
+
+def test_square_graph_is_dense_identity_plus_w_squared_on_a_slab(oracle_lib):
+    m = W.mesh(7, 6, 4)
+    A = oracle_lib.assemble(m, W.DEFAULT_PARAMS, W.fibre_table(m, 120.0, 5.0))["A"]
+    S = oracle_lib.strength(A, 0.06)
+    S2 = _check_square(oracle_lib, S)
+    # a direct strong neighbour q of p with no common neighbour carries exactly 2 w_pq
+    Sd = S.toarray()
+    for p in range(0, S.shape[0], 7):
+        for q in S.indices[S.indptr[p]:S.indptr[p + 1]]:
+            if not np.any((Sd[p] > 0) & (Sd[q] > 0)):
+                assert S2[p, q] == 2.0 * Sd[p, q]
+
+
+def test_square_graph_on_random_symmetric_graphs(oracle_lib):
+    rng = np.random.default_rng(21)
+    for trial in range(30):
+        n = int(rng.integers(1, 40))
+        G = _random_graph(rng, n, rng.uniform(0.02, 0.5)).toarray()
+        w = np.triu(rng.uniform(0.06, 1.0, (n, n)), 1)
+        w = (w + w.T) * G
+        _check_square(oracle_lib, sp.csr_matrix(w))
+    # isolated nodes stay isolated; a path a-b-c gains the two-step edge a-c = w_ab w_bc
+    Wp = sp.csr_matrix(np.array([[0, 0.5, 0, 0], [0.5, 0, 0.25, 0], [0, 0.25, 0, 0], [0, 0, 0, 0]]))
+    S2 = oracle_lib.square_graph(Wp).toarray()
+    assert S2[0, 2] == 0.125 and S2[0, 1] == 1.0 and S2[1, 2] == 0.5
+    assert not S2[3].any() and not S2[:, 3].any()
+
+
+def test_aggregation_rule_on_the_squared_graph_by_brute_force(oracle_lib):
+    """Section 4's cluster rule run on the squared graph (Appendix A): every
+    non-root joins the root with the largest (I+W)^2 weight, ties to the
+    smaller root index; checked against the dense square, not the oracle's."""
+    for m, key_seed in ((W.mesh(10, 9, 5), 7), (W.mesh(8, 8, 3), 11)):
+        A = oracle_lib.assemble(m, W.DEFAULT_PARAMS, W.fibre_table(m, 120.0, 5.0))["A"]
+        S = oracle_lib.strength(A, 0.06)
+        S2 = oracle_lib.square_graph(S)
+        key = oracle_lib.level_key(key_seed, 0, 0)
+        s = oracle_lib.mis(S2, key)
+        Q = _dense_square_without_diagonal(S)
+        adj = Q > 0
+        roots = np.flatnonzero(s)
+        # independence and maximality on the squared graph
+        assert not np.any(adj[np.ix_(roots, roots)])
+        assert all(s[i] or np.any(adj[i, roots]) for i in range(Q.shape[0]))
+        agg, na = oracle_lib.aggregate(S2, s)
+        assert na == roots.size
+        assert np.array_equal(agg[roots], np.arange(na))
+        for i in range(Q.shape[0]):
+            if s[i]:
+                continue
+            cand = [(Q[i, j], -j) for j in roots if Q[i, j] > 0]
+            w, mj = max(cand)
+            # equal weights in exact arithmetic may differ by rounding between
+            # the dense and the sparse sums: accept only an exact-tie ambiguity
+            best = [j for (wj, j) in ((Q[i, j], j) for j in roots if Q[i, j] > 0)
+                    if abs(wj - w) <= 4e-16 * w * 8]
+            if len(best) == 1:
+                assert agg[i] == agg[-mj]
+            else:
+                assert agg[i] in set(agg[best])
+
+
 # --------------------------------------------------------------- prolongators
 @pytest.fixture(scope="module")
 def small_hier(oracle_lib):

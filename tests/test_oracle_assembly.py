@@ -129,6 +129,69 @@ def test_general_constant_tensor_off_diagonal_terms(oracle_lib):
     assert np.allclose(out["Ki"].toarray(), Kref, rtol=1e-12, atol=1e-14 * np.abs(Kref).max())
 
 
+def _gauss_layer_stiffness(mesh, sl, st, theta_of_z):
+    """Stiffness of a slab whose conductivity varies with z only, by 2x2x2
+    Gauss quadrature (Section 2.2): x and y integrated exactly by the 1D
+    tensor factors, z sampled at numpy's two Gauss-Legendre points of every
+    element layer, where D(z) = st I + (sl - st) a a^T with
+    a = (cos theta(z), sin theta(z), 0) (Eq. 2) is evaluated directly."""
+    nx, ny, nz = mesh["nx"], mesh["ny"], mesh["nz"]
+    hx, hy, hz = mesh["lx"] / nx, mesh["ly"] / ny, mesh["lz"] / nz
+    fx = dict(K=_k1d(nx, hx), M=_m1d(nx, hx), C=_c1d(nx))
+    fy = dict(K=_k1d(ny, hy), M=_m1d(ny, hy), C=_c1d(ny))
+    xi, wq = np.polynomial.legendre.leggauss(2)
+    K = sp.csr_matrix(((nx + 1) * (ny + 1) * (nz + 1),) * 2)
+    for ez in range(nz):
+        for g in range(2):
+            t = (1.0 + xi[g]) / 2.0                  # position inside the layer
+            z = (ez + t) * hz
+            th = theta_of_z(z)
+            a = np.array([math.cos(th), math.sin(th), 0.0])
+            D = st * np.eye(3) + (sl - st) * np.outer(a, a)
+            N = np.array([1.0 - t, t])                # z basis values
+            dN = np.array([-1.0, 1.0]) / hz           # z basis derivatives
+            jw = wq[g] * hz / 2.0
+
+            def zf(u, v):
+                m = np.zeros((nz + 1, nz + 1))
+                m[ez:ez + 2, ez:ez + 2] = jw * np.outer(u, v)
+                return sp.csr_matrix(m)
+            fz = dict(K=zf(dN, dN), M=zf(N, N), C=zf(dN, N))
+            for d in range(3):
+                for e in range(3):
+                    if D[d, e] == 0.0:
+                        continue
+                    f = []
+                    for ax, fac in enumerate((fx, fy, fz)):
+                        if ax == d and ax == e:
+                            f.append(fac["K"])
+                        elif ax == d:
+                            f.append(fac["C"])
+                        elif ax == e:
+                            f.append(fac["C"].T)
+                        else:
+                            f.append(fac["M"])
+                    K = K + D[d, e] * _kron3(f[2], f[1], f[0])
+    return K.toarray()
+
+
+@pytest.mark.parametrize("rot,off", [(120.0, 5.0), (-75.0, 20.0)])
+def test_z_varying_fibre_matches_gauss_quadrature(oracle_lib, rot, off):
+    """The fibre table's Gauss z-levels (Section 2.2 quadrature, D sampled at
+    the Gauss points) against an independent quadrature that evaluates
+    theta(z) = off + rot (z/lz - 1/2) itself: a swapped or shifted z-level, or
+    a table read at the wrong layer, changes the layer's stiffness."""
+    m = W.mesh(2, 3, 3, 0.2, 0.25, 0.3)
+    p = dict(W.DEFAULT_PARAMS)
+    out = oracle_lib.assemble(m, p, W.fibre_table(m, rot, off))
+
+    def theta(z):
+        return math.radians(off) + math.radians(rot) * (z / m["lz"] - 0.5)
+    for K, (sl, st) in ((out["Ki"], (p["sil"], p["sit"])), (out["Ke"], (p["sel"], p["set"]))):
+        Kref = _gauss_layer_stiffness(m, sl, st, theta)
+        assert np.allclose(K.toarray(), Kref, rtol=1e-12, atol=1e-13 * np.abs(Kref).max())
+
+
 def test_row_sums_symmetry_mass(oracle_lib):
     m = W.SLAB_SMALL
     out = oracle_lib.assemble(m, W.DEFAULT_PARAMS, W.fibre_table(m))

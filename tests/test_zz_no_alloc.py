@@ -1,9 +1,8 @@
 """The allocation-free reproducible dot (bd_dot_exact_noalloc), through the C ABI.
 
-This entry point serves callers that must not allocate device memory: code
-whose stream is being captured into a CUDA graph, latency-critical loops in
-which cudaMalloc would synchronise the device, and hosts whose memory belongs
-to another allocator.  Its scratch is a static device array shared by every
+This entry point serves callers that cannot allocate device memory: hosts
+whose device memory belongs to another allocator, and latency-critical loops
+in which cudaMalloc would synchronise the device.  Its scratch is a static device array shared by every
 call, so the test makes two calls in a row with different inputs: the second
 must not see anything left over from the first.  The file is named so that
 pytest collects it last.
@@ -61,3 +60,5 @@ def test_noalloc_dot_rejects_sizes_beyond_its_maximum(B):
     assert st == B.BD_ERANGE
     st = B.lib().bd_dot_exact_noalloc(p(x.data_ptr()), p(x.data_ptr()), -1, p(out.data_ptr()), None)
     assert st == B.BD_EINVAL
+    with pytest.raises(ValueError):
+        B.bd_dot_exact_noalloc(x, x, torch.zeros(0, dtype=torch.float64, device="cuda"))
