@@ -49,11 +49,14 @@ def parse_args(argv=None):
     ap.add_argument("--time-steps", type=int, default=T_STEPS)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-steps", type=int, default=2)
     ap.add_argument("--square-levels", type=int, default=None)
     ap.add_argument("--theta", type=float, default=None)
+    ap.add_argument("--form-steps", type=int, default=5,
+                    help="steps of each grown form measured after the timed region")
+    ap.add_argument("--no-grown-forms", action="store_true",
+                    help="skip the batched and served forms after the timed region")
     ap.add_argument("--no-fp32-form", action="store_true",
-                    help="skip the untimed side measurement of the FP32 V-cycle form")
+                    help="skip every grown form measured after the timed region")
     ap.add_argument("--autotune", type=int, choices=(0, 1), default=None,
                     help="1: time the candidate forms of the block operators at setup "
                          "(amg_options.autotune = 1); 0: the row-count and row-length rule.  "
@@ -333,9 +336,12 @@ def run_ours(args):
     elapsed_ms = max_over_ranks(dist, t0.elapsed_time(t1), True)
     value = replica_throughput(world, args.steps, T, elapsed_ms)
 
-    # the precision form beside the FP64 line (same workload and protocol,
-    # FP32 V-cycle inside the FP64 flexible CG; rank 0, after the timed region)
-    fp32_form = None
+    # The grown forms beside the FP64 line (rank 0, after the timed region;
+    # each timed by CUDA events or the server's clock, with its own clocks
+    # record): the FP32 V-cycle form on the same workload and protocol, the
+    # 64-slab batch (FP64 and FP32 V-cycle, batched vs one solve at a time) and
+    # the served form (p50/p99, batched FP32 vs sequential FP64).
+    forms = None
     if rank == 0 and args.precision == "fp64" and not args.no_fp32_form:
         a32 = argparse.Namespace(**{**vars(args), "precision": "fp32"})
         opts32 = amg_opts(B, a32)
@@ -357,13 +363,25 @@ def run_ours(args):
             return out
 
         step32()
-        runs = [step32() for _ in range(max(1, min(args.steps, 2)))]
+        ck = ClockSampler(local)
+        ck.start()
+        runs = [step32() for _ in range(max(1, args.form_steps))]
+        clk32 = ck.stop()
         ms_step = statistics.mean(r[0] for r in runs)
-        fp32_form = {"value": T / (ms_step / 1e3), "unit": "solves/s",
-                     "solve_only_solves_per_s": T / (statistics.mean(r[1] for r in runs) / 1e3),
-                     "mean_pcg_iters": statistics.mean(r[2]["total_iters"] / T for r in runs),
-                     "max_true_rel_res": max(r[2]["true_rel_res"] for r in runs),
-                     "steps": len(runs), "dtype": "f64 CG, FP32 V-cycle"}
+        forms = {"fp32_vcycle": {
+            "value": T / (ms_step / 1e3), "unit": "solves/s",
+            "speedup_vs_fp64": (T / (ms_step / 1e3)) / value,
+            "solve_only_solves_per_s": T / (statistics.mean(r[1] for r in runs) / 1e3),
+            "mean_pcg_iters": statistics.mean(r[2]["total_iters"] / T for r in runs),
+            "max_true_rel_res": max(r[2]["true_rel_res"] for r in runs),
+            "steps": len(runs), "dtype": "f64 CG, FP32 V-cycle", "timing": "CUDA events",
+            "clocks": clk32}}
+        if not args.no_grown_forms:
+            ab = argparse.Namespace(**{**vars(args), "mode": "batch", "coarse_eq_limit": None,
+                                       "autotune": 1})
+            forms["batch"] = {prec: batch_measure(ab, prec, args.form_steps, 2, stream)
+                              for prec in ("fp64", "fp32")}
+            forms["serve"] = serve_measure(ab, "fp32", args.requests)
 
     # untimed: per-step device time of the solve phase (host-driven loop with
     # CUDA events around every step), per PCG iteration
@@ -468,7 +486,7 @@ def run_ours(args):
                    "levels": rec.get("levels"), "operator_complexity": rec.get("op_complexity"),
                    "lanes_A_R_P": rec.get("lanes"),
                    "breakdown_us_per_pcg_iteration": breakdown,
-                   "fp32_vcycle_form": fp32_form,
+                   "forms": forms,
                    "amg_options": {k: getattr(amg_opts(B, args), k) for k in
                                    ("theta", "square_levels", "coarse_eq_limit", "cheb_degree",
                                     "precision", "autotune")}},
@@ -485,90 +503,115 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------------ oracle (CPU)
-def oracle_sample(mesh, fib, stim, n_steps: int, opts: dict):
-    """Assembly + setup of the full workload, then n_steps time steps; returns
-    (t_setup_s, mean_step_s, mean_iters)."""
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_protocol(mesh, fib, stim, opts: dict, warm: int, timed: int, one_core_steps: int = 1):
+    """The oracle on the host cores: assembly + setup on one thread, `warm`
+    untimed time steps, then `timed` time steps on all cores (the solve
+    phase's independent loops in parallel; results bitwise those of one
+    thread).  The first `one_core_steps` of the timed steps are replayed on
+    one thread from a snapshot of the state, so both figures cover the same
+    steps.  Returns a dict of times (s), iterations and thread counts."""
     import numpy as np
 
     import oracle
     from paper_2311_13914_gb300 import workloads as W
 
+    oracle.build()
+    threads = max(1, os.cpu_count() or 1)
     p = W.DEFAULT_PARAMS
+    oracle.set_threads(1)
     t0 = time.perf_counter()
     o = oracle.assemble(mesh, p, fib)
     H = oracle.Hierarchy(o["A"], **opts)
     t_setup = time.perf_counter() - t0
+    try:
+        oracle.set_threads(threads)
+    except RuntimeError:   # built without OpenMP
+        threads = 1
     N = W.n_nodes(mesh)
     v, ue, w = np.zeros(N), np.zeros(N), np.zeros(N)
-    times, its = [], []
-    for k in range(n_steps):
+
+    def step(k, state):
         Iapp = stim if k * p["dt"] < STIM_MS else np.zeros(N)
+        return H.bd_step(o["M"], p, Iapp, *state)["iters"]
+
+    for k in range(warm):
+        step(k, (v, ue, w))
+    snap = (v.copy(), ue.copy(), w.copy())
+    its = []
+    s0 = time.perf_counter()
+    for k in range(warm, warm + timed):
+        its.append(step(k, (v, ue, w)))
+    t_all = (time.perf_counter() - s0) / max(timed, 1)
+    t_one = None
+    n1 = min(one_core_steps, timed)
+    if n1 > 0:
+        oracle.set_threads(1)
         s0 = time.perf_counter()
-        info = H.bd_step(o["M"], p, Iapp, v, ue, w)
-        times.append(time.perf_counter() - s0)
-        its.append(info["iters"])
-    return t_setup, statistics.mean(times), statistics.mean(its)
+        for k in range(warm, warm + n1):
+            step(k, snap)
+        t_one = (time.perf_counter() - s0) / n1
+        oracle.set_threads(threads)
+    return {"t_setup": t_setup, "t_step": t_all, "t_step_one_core": t_one, "iters": its,
+            "threads": threads, "warm": warm, "timed": timed, "one_core_steps": n1}
+
+
+def cpu_record(r: dict, T: int) -> dict:
+    """cpu_baseline entry from an oracle_protocol result: solves/s of the
+    whole simulation (setup + T steps, extrapolated from the timed steps)."""
+    value = T / (r["t_setup"] + T * r["t_step"])
+    one = None
+    if r["t_step_one_core"] is not None:
+        one = {"value": T / (r["t_setup"] + T * r["t_step_one_core"]), "unit": "solves/s",
+               "solve_phase_solves_per_s": 1.0 / r["t_step_one_core"],
+               "steps": r["one_core_steps"]}
+    its = statistics.mean(r["iters"]) if r["iters"] else 0.0
+    return {"value": value, "unit": "solves/s", "cores": r["threads"], "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "solve_phase_solves_per_s": 1.0 / r["t_step"],
+            "one_core": one,
+            "sample": (f"full-size assembly + setup on one thread ({r['t_setup']:.1f} s), "
+                       f"{r['warm']} untimed time steps, then time steps {r['warm']}.."
+                       f"{r['warm'] + r['timed'] - 1} on {r['threads']} threads "
+                       f"({r['t_step']:.2f} s each, {its:.1f} PCG its), extrapolated to {T} steps; "
+                       f"one_core: the first {r['one_core_steps']} of those steps replayed on one "
+                       f"thread ({(r['t_step_one_core'] or 0):.2f} s each); C oracle")}
 
 
 def cpu_baseline(args):
-    import oracle
-
-    oracle.build()
     mesh, fib, stim, desc = workload(args.workload)
-    T = args.time_steps
-    t_setup, t_step, its = oracle_sample(mesh, fib, stim, max(1, args.cpu_sample_steps),
-                                         oracle_opts(args))
-    value = T / (t_setup + T * t_step)
-    return {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": (f"full-size assembly + setup ({t_setup:.1f} s) and the first "
-                       f"{max(1, args.cpu_sample_steps)} time steps ({t_step:.1f} s each, "
-                       f"{its:.1f} PCG its), extrapolated to {T} steps; single-threaded C oracle")}
+    r = oracle_protocol(mesh, fib, stim, oracle_opts(args), args.warmup, args.steps,
+                        one_core_steps=1)
+    return cpu_record(r, args.time_steps)
 
 
 def run_reference(args):
     """The oracle as it stands, on the host cores.  Each step = one time step
     of the same workload; assembly + setup are timed once and amortised over
     the simulation's time steps so the unit matches the CUDA arm."""
-    import numpy as np
-
-    import oracle
-    from paper_2311_13914_gb300 import workloads as W
-
     rank, local, world = dist_info()
     if rank != 0:
         return None
-    oracle.build()
     mesh, fib, stim, desc = workload(args.workload)
     T = args.time_steps
-    p = W.DEFAULT_PARAMS
-    t0 = time.perf_counter()
-    o = oracle.assemble(mesh, p, fib)
-    H = oracle.Hierarchy(o["A"], **oracle_opts(args))
-    t_setup = time.perf_counter() - t0
-    N = W.n_nodes(mesh)
-    v, ue, w = np.zeros(N), np.zeros(N), np.zeros(N)
-    k = 0
-
-    def step():
-        nonlocal k
-        Iapp = stim if k * p["dt"] < STIM_MS else np.zeros(N)
-        H.bd_step(o["M"], p, Iapp, v, ue, w)
-        k += 1
-
-    for _ in range(args.warmup):
-        step()
-    s0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    t_step = (time.perf_counter() - s0) / max(args.steps, 1)
-    value = T / (t_setup + T * t_step)
-    cpu = {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-           "sample": (f"assembly + setup once ({t_setup:.1f} s) and {args.steps} timed time "
-                      f"steps ({t_step:.2f} s each) of the full workload, extrapolated to "
-                      f"{T} steps")}
+    r = oracle_protocol(mesh, fib, stim, oracle_opts(args), args.warmup, args.steps,
+                        one_core_steps=1)
+    cpu = cpu_record(r, T)
+    value = cpu["value"]
     return {"impl": "reference", "metric": "AMG-PCG solves/sec to rtol 1e-8 (coupled Bidomain, "
             "paper-size slab, time stepping)", "value": value, "unit": "solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["t_step"] * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": desc.format(T=T)},
             "cpu_baseline": cpu,
@@ -596,34 +639,35 @@ def serve_requests(n: int, seed: int = 3):
     return out
 
 
-def run_serve(args):
+def serve_measure(args, precision: str, n_requests: int) -> dict:
+    """Continuous batching of seeded simulations (serve_requests): closed loop
+    (all submitted at t = 0) for capacity, then Poisson arrivals at 0.7x each
+    form's own capacity for p50/p99 latency; the batched form (up to 16
+    active) against sequential FP64 (one at a time).  Latencies are the
+    server's submit-to-done times."""
     import numpy as np
-    import torch
 
     from paper_2311_13914_gb300 import binding as B
     from paper_2311_13914_gb300 import workloads as W
 
-    rank, local, world = dist_info()
-    torch.cuda.set_device(local)
-    B.lib()
     p = W.DEFAULT_PARAMS
-    reqs = serve_requests(args.requests)
+    reqs = serve_requests(n_requests)
     total_solves = sum(r[3] for r in reqs)
 
-    def run(precision, max_active, arrivals=None):
-        srv = B.bd_server_create(B.bd_server_options_default(precision=precision,
-                                                             max_active=max_active))
+    def run(prec, max_active, arrivals=None, subset=None):
+        rs = reqs if subset is None else reqs[:subset]
+        srv = B.bd_server_create(B.bd_server_options_default(precision=prec, max_active=max_active))
         ids, t0 = [], time.perf_counter()
         nxt = 0
         while True:
             now = time.perf_counter() - t0
-            while nxt < len(reqs) and (arrivals is None or arrivals[nxt] <= now):
-                m, fib, stim, steps = reqs[nxt]
+            while nxt < len(rs) and (arrivals is None or arrivals[nxt] <= now):
+                m, fib, stim, steps = rs[nxt]
                 ids.append(B.bd_server_submit(srv, m, p, fib, stim, STIM_MS, steps))
                 nxt += 1
             a, q = B.bd_server_tick(srv)
             if a == 0 and q == 0:
-                if nxt >= len(reqs):
+                if nxt >= len(rs):
                     break
                 time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
         wall = time.perf_counter() - t0
@@ -633,11 +677,14 @@ def run_serve(args):
         srv.close()
         return wall, lat
 
-    prec = 1 if args.precision == "fp32" else 0
-    run(0, 1, None)  # warm-up
+    prec = 1 if precision == "fp32" else 0
+    run(0, 1, None, subset=4)      # warm-up (both forms' kernels)
+    run(prec, 16, None, subset=4)
+    clocks = ClockSampler(0)
+    clocks.start()
     # closed loop (every request submitted at t = 0): capacity in solves/s
-    seq_wall, seq_lat = run(0, 1, None)
-    cap_wall, cap_lat = run(prec, 16, None)
+    seq_wall, _ = run(0, 1, None)
+    cap_wall, _ = run(prec, 16, None)
     seq_rate, cap_rate = total_solves / seq_wall, total_solves / cap_wall
     # open loop: Poisson arrivals at 0.7x each form's own request capacity
     rng = np.random.Generator(np.random.PCG64(3))
@@ -652,43 +699,58 @@ def run_serve(args):
     _, lat_b = run(prec, 16, arr_b)
     arr_s, lam_s = poisson(seq_wall)
     _, lat_s = run(0, 1, arr_s)
+    clk = clocks.stop()
     pct = lambda a, q: float(np.percentile(a, q))  # noqa: E731
+    return {"workload": f"{len(reqs)} requests, slabs 32x32x8..192x192x48 (4:4:1), 20-200 "
+                        f"RM time steps each, {total_solves} solves, seed 3",
+            "dtype": "f64 (FP32 V-cycle)" if prec else "f64",
+            "batched_closed_loop_solves_per_s": cap_rate,
+            "sequential_fp64_closed_loop_solves_per_s": seq_rate,
+            "speedup_vs_sequential_fp64": cap_rate / seq_rate,
+            "batched_poisson_rate_req_per_s": lam_b,
+            "batched_p50_latency_ms": pct(lat_b, 50),
+            "batched_p99_latency_ms": pct(lat_b, 99),
+            "sequential_fp64_poisson_rate_req_per_s": lam_s,
+            "sequential_fp64_p50_latency_ms": pct(lat_s, 50),
+            "sequential_fp64_p99_latency_ms": pct(lat_s, 99),
+            "max_active": 16, "timing": "host wall clock around the server's ticks",
+            "clocks": clk}
+
+
+def run_serve(args):
+    import torch
+
+    from paper_2311_13914_gb300 import binding as B
+
+    rank, local, world = dist_info()
+    torch.cuda.set_device(local)
+    B.lib()
+    r = serve_measure(args, args.precision, args.requests)
     return {"metric": "served AMG-PCG solves/sec to rtol 1e-8 (continuous batching of simulations)",
-            "value": cap_rate, "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
-            "vs_baseline": None, "dtype": "f64 (FP32 V-cycle)" if prec else "f64",
+            "value": r["batched_closed_loop_solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "higher_is_better": True, "vs_baseline": None, "dtype": r["dtype"],
             "data": "synthetic",
-            "config": {"workload": f"{len(reqs)} requests, slabs 32x32x8..192x192x48 (4:4:1), 20-200 "
-                                   f"RM time steps each, {total_solves} solves, seed 3",
-                       "batched_closed_loop_solves_per_s": cap_rate,
-                       "sequential_fp64_closed_loop_solves_per_s": seq_rate,
-                       "speedup_vs_sequential_fp64": cap_rate / seq_rate,
-                       "batched_poisson_rate_req_per_s": lam_b,
-                       "batched_p50_latency_ms": pct(lat_b, 50),
-                       "batched_p99_latency_ms": pct(lat_b, 99),
-                       "sequential_fp64_poisson_rate_req_per_s": lam_s,
-                       "sequential_fp64_p50_latency_ms": pct(lat_s, 50),
-                       "sequential_fp64_p99_latency_ms": pct(lat_s, 99),
-                       "max_active": 16}}
+            "config": {k: v for k, v in r.items() if k not in ("clocks", "dtype")},
+            "clocks": r["clocks"]}
 
 
-def run_batch(args):
+def batch_measure(args, precision: str, steps: int, warmup: int, stream=None) -> dict:
     """64 uneven slabs (nx, ny ~ U{16..64}, nz ~ U{8..16}, seed 2), hierarchies
     resident: every step solves all 64 systems, once as one batched graph
-    launch and once one amg_solve at a time (each its own graph launch)."""
+    launch and once one amg_solve at a time (each its own graph launch).
+    Device time by CUDA events on the solving stream."""
     import torch
 
     from paper_2311_13914_gb300 import binding as B
     from paper_2311_13914_gb300 import workloads as W
 
-    rank, local, world = dist_info()
-    torch.cuda.set_device(local)
-    B.lib()
+    a = argparse.Namespace(**{**vars(args), "precision": precision})
     slabs = W.batch_slabs(64, seed=2)
-    stream = torch.cuda.Stream()
+    stream = stream or torch.cuda.Stream()
     hs, fs, xs = [], [], []
     for k, (m, p, fib) in enumerate(slabs):
         sysh = B.bd_assemble(m, p, fib, stream=stream)
-        h = B.amg_setup(sysh, amg_opts(B, args), stream=stream)
+        h = B.amg_setup(sysh, amg_opts(B, a), stream=stream)
         n = 2 * W.n_nodes(m)
         hs.append((sysh, h))
         fs.append(torch.tensor(W.rhs(n, k), device="cuda"))
@@ -705,38 +767,56 @@ def run_batch(args):
     def batched():
         return sum(i["iters"] for i in B.amg_batch_solve(b, fs, xs, stream=stream))
 
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(warmup, 1)):
         sequential()
         batched()
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    t = {}
-    its = {}
+    t, its = {}, {}
     for name, fn in (("sequential", sequential), ("batched", batched)):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        its[name] = sum(fn() for _ in range(args.steps))
+        e0.record(stream)
+        its[name] = sum(fn() for _ in range(steps))
+        e1.record(stream)
         torch.cuda.synchronize()
-        t[name] = time.perf_counter() - t0
+        t[name] = e0.elapsed_time(e1) / 1e3
     clk = clocks.stop()
-    n_solves = len(slabs) * args.steps
+    n_solves = len(slabs) * steps
     rate = {k: n_solves / v for k, v in t.items()}
     b.close()
+    for sysh, h in hs:
+        h.close()
+        sysh.close()
     unknowns = [2 * W.n_nodes(m) for m, _, _ in slabs]
-    return {"metric": "AMG-PCG solves/sec to rtol 1e-8, 64 uneven slabs per step (batched form)",
-            "value": rate["batched"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t["batched"] / args.steps,
-            "higher_is_better": True, "vs_baseline": None,
-            "dtype": "f64 (FP32 V-cycle)" if args.precision == "fp32" else "f64", "data": "synthetic",
-            "config": {"workload": f"64 slabs, {min(unknowns)}..{max(unknowns)} unknowns "
-                                   f"({sum(unknowns)} in all), one solve each per step, seed 2",
-                       "batched_solves_per_s": rate["batched"],
-                       "one_at_a_time_solves_per_s": rate["sequential"],
-                       "speedup": rate["batched"] / rate["sequential"],
-                       "mean_pcg_iters": its["batched"] / n_solves,
-                       "amg_options": {k: getattr(amg_opts(B, args), k) for k in
-                                       ("theta", "square_levels", "precision", "autotune")}},
+    return {"batched_solves_per_s": rate["batched"], "one_at_a_time_solves_per_s": rate["sequential"],
+            "speedup": rate["batched"] / rate["sequential"],
+            "mean_pcg_iters": its["batched"] / n_solves, "steps": steps,
+            "ms_per_step": 1e3 * t["batched"] / steps,
+            "workload": f"64 slabs, {min(unknowns)}..{max(unknowns)} unknowns "
+                        f"({sum(unknowns)} in all), one solve each per step, seed 2",
+            "dtype": "f64 (FP32 V-cycle)" if precision == "fp32" else "f64",
+            "amg_options": {k: getattr(amg_opts(B, a), k) for k in
+                            ("theta", "square_levels", "coarse_eq_limit", "precision", "autotune")},
             "clocks": clk}
+
+
+def run_batch(args):
+    import torch
+
+    from paper_2311_13914_gb300 import binding as B
+
+    rank, local, world = dist_info()
+    torch.cuda.set_device(local)
+    B.lib()
+    r = batch_measure(args, args.precision, args.steps, args.warmup)
+    return {"metric": "AMG-PCG solves/sec to rtol 1e-8, 64 uneven slabs per step (batched form)",
+            "value": r["batched_solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "vs_baseline": None, "dtype": r["dtype"], "data": "synthetic",
+            "config": {k: v for k, v in r.items() if k not in ("clocks", "dtype", "steps", "ms_per_step")},
+            "clocks": r["clocks"]}
 
 
 def run_sweep(args):

@@ -118,6 +118,13 @@ typedef struct {
 const char *bd_strerror(int status);
 /* Number of CUDA kernels this library has launched in the process so far. */
 long long bd_launch_count(void);
+/* Sparse matrix products the hierarchy setup has formed in the process so far,
+ * by path: *hash_calls through the warp-per-row shared-memory hash (rows of at
+ * most 4096 block products), *dense_calls through the block-per-row dense
+ * accumulator (longer rows).  Both paths add every entry in ascending middle
+ * index, so the path never changes a bit; the counts let a test show which
+ * path a setup exercised.  Errors: BD_EINVAL (NULL). */
+int bd_spgemm_path_counts(long long *hash_calls, long long *dense_calls);
 void amg_options_default(amg_options *o);
 void solve_options_default(solve_options *o);
 void bd_rm_params_default(bd_rm_params *p);

@@ -44,7 +44,13 @@ def build(force: bool = False) -> str:
         os.path.getmtime(_SRC), os.path.getmtime(_HDR)) > os.path.getmtime(_SO)
     if stale:
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        try:
+            # the solve phase's independent loops in parallel (bitwise the same
+            # results for any thread count); serial if OpenMP is unavailable
+            subprocess.check_call(["gcc", *CFLAGS, "-fopenmp", "-o", tmp, _SRC, "-lm"],
+                                  stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -81,6 +87,8 @@ def lib():
             L = C.CDLL(build())
             L.oc_csr_free.argtypes = [_P(_CSR)]
             L.oc_dot_exact.argtypes = [_i64, _vp, _vp]
+            L.oc_set_threads.argtypes = [_i]
+            L.oc_get_threads.argtypes = []
             L.oc_dot_exact.restype = _d
             L.oc_sum_exact.argtypes = [_i64, _vp]
             L.oc_sum_exact.restype = _d
@@ -177,6 +185,15 @@ def _check(rc: int, what: str):
 
 
 # ---------------------------------------------------------------- primitives
+def set_threads(n: int) -> None:
+    """Threads of the oracle's solve phase (results do not depend on it)."""
+    _check(lib().oc_set_threads(int(n)), "set_threads")
+
+
+def get_threads() -> int:
+    return lib().oc_get_threads()
+
+
 def dot_exact(x, y) -> float:
     x, y = _f64(x), _f64(y)
     return lib().oc_dot_exact(x.size, _ptr(x), _ptr(y))

@@ -11,11 +11,39 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OC_EINVAL (-1)
 #define OC_ENOMEM (-2)
 #define OC_EBREAK (-3)
 #define OC_ENOTCONV (-4)
+
+/* Threads of the solve phase.  Only loops whose iterations are independent
+ * (SpMV rows, element-wise vector updates, per-node time-step updates) run in
+ * parallel; every reduction (dot products, means) stays a serial loop in
+ * index order, so the results are bitwise the same for any thread count.
+ * Built without OpenMP the oracle is serial and reports one thread. */
+int oc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n < 1) return OC_EINVAL;
+    omp_set_num_threads(n);
+    return 0;
+#else
+    return n == 1 ? 0 : OC_EINVAL;
+#endif
+}
+
+int oc_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 void oc_csr_free(oc_csr *a)
 {
@@ -367,6 +395,7 @@ int oc_assemble(int nx, int ny, int nz, double lx, double ly, double lz,
  * ====================================================================== */
 int oc_spmv(const oc_csr *A, const double *x, double *y)
 {
+#pragma omp parallel for schedule(static) if (A->nrows > 4096)
     for (int i = 0; i < A->nrows; i++) {
         double s = 0.0;
         for (int64_t t = A->rp[i]; t < A->rp[i + 1]; t++) s = s + A->v[t] * x[A->ci[t]];
@@ -1031,6 +1060,7 @@ int oc_chebyshev(const oc_csr *A, const double *f, double *x, int x_is_zero,
         free(r); free(d); free(q); free(D);
         return OC_ENOMEM;
     }
+#pragma omp parallel for schedule(static) if (n > 4096)
     for (int i = 0; i < n; i++) {
         int64_t t = csr_find(A, i, i);
         D[i] = A->v[t];
@@ -1038,20 +1068,25 @@ int oc_chebyshev(const oc_csr *A, const double *f, double *x, int x_is_zero,
     double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
     double sigma = theta / delta, rho = 1.0 / sigma;
     if (x_is_zero) {
+#pragma omp parallel for schedule(static) if (n > 4096)
         for (int i = 0; i < n; i++) {
             x[i] = 0.0;
             r[i] = f[i];
         }
     } else {
         oc_spmv(A, x, q);
+#pragma omp parallel for schedule(static) if (n > 4096)
         for (int i = 0; i < n; i++) r[i] = f[i] - q[i];
     }
+#pragma omp parallel for schedule(static) if (n > 4096)
     for (int i = 0; i < n; i++) d[i] = r[i] / D[i] / theta;
     for (int k = 1; k <= degree; k++) {
+#pragma omp parallel for schedule(static) if (n > 4096)
         for (int i = 0; i < n; i++) x[i] = x[i] + d[i];
         if (k == degree) break;
         oc_spmv(A, d, q);
         double rho1 = 1.0 / (2.0 * sigma - rho);
+#pragma omp parallel for schedule(static) if (n > 4096)
         for (int i = 0; i < n; i++) {
             r[i] = r[i] - q[i];
             d[i] = rho1 * rho * d[i] + (2.0 * rho1 / delta) * (r[i] / D[i]);
@@ -1104,10 +1139,12 @@ static int vcycle_level(const oc_hier *h, int l, const double *f, double *u)
     }
     oc_chebyshev(A, f, u, 1, h->cheb_degree, lo, hi);         /* pre-smoothing */
     oc_spmv(A, u, r);
+#pragma omp parallel for schedule(static) if (n > 4096)
     for (int i = 0; i < n; i++) r[i] = f[i] - r[i];            /* r = f - A u */
     oc_spmv(&h->R[l], r, rc);                                  /* r_c = R r  */
     int rc_ = vcycle_level(h, l + 1, rc, ec);                  /* recursion  */
     oc_spmv(&h->P[l], ec, e);                                  /* e = P e_c  */
+#pragma omp parallel for schedule(static) if (n > 4096)
     for (int i = 0; i < n; i++) u[i] = u[i] + e[i];            /* correction */
     oc_chebyshev(A, f, u, 0, h->cheb_degree, lo, hi);          /* post-smoothing */
     free(r); free(rc); free(ec); free(e);
@@ -1168,6 +1205,7 @@ int oc_pcg(const oc_hier *h, const double *f_in, double *x, int warm, double rto
         for (int i = 0; i < n; i++) x[i] = 0.0;
     } else {
         oc_spmv(A, x, q);
+#pragma omp parallel for schedule(static) if (n > 4096)
         for (int i = 0; i < n; i++) r[i] = f[i] - q[i];
         rr = sqrt(dot(n, r, r));
         if (rr > rtol * nf) {
@@ -1184,6 +1222,7 @@ int oc_pcg(const oc_hier *h, const double *f_in, double *x, int warm, double rto
                     break;
                 }
                 double alpha = rz / pq;
+#pragma omp parallel for schedule(static) if (n > 4096)
                 for (int i = 0; i < n; i++) {
                     x[i] = x[i] + alpha * p[i];
                     r[i] = r[i] - alpha * q[i];
@@ -1198,6 +1237,7 @@ int oc_pcg(const oc_hier *h, const double *f_in, double *x, int warm, double rto
                 project_u(n, z);
                 double rz1 = dot(n, r, z);
                 double beta = rz1 / rz;
+#pragma omp parallel for schedule(static) if (n > 4096)
                 for (int i = 0; i < n; i++) p[i] = z[i] + beta * p[i];
                 rz = rz1;
             }
@@ -1237,6 +1277,7 @@ int oc_bd_step(const oc_hier *h, const double *M, int N, double chi, double cm,
         return OC_ENOMEM;
     }
     double c = (chi * cm) / dt;
+#pragma omp parallel for schedule(static) if (N > 4096)
     for (int k = 0; k < N; k++) {
         double vk = v[k];
         double wn = (w[k] + dt * rm->eta2 * vk / rm->vp) / (1.0 + dt * rm->eta2 * rm->eta3);

@@ -35,6 +35,13 @@ typedef struct {
 
 void oc_csr_free(oc_csr *a);
 
+/* Threads of the solve phase (OpenMP build): only loops with independent
+ * iterations run in parallel and every reduction stays serial, so results are
+ * bitwise independent of the thread count.  oc_set_threads returns nonzero if
+ * the count cannot be set (n < 1, or n > 1 in a build without OpenMP). */
+int oc_set_threads(int n);
+int oc_get_threads(void);
+
 /* Correctly rounded sum of the rounded products x[i]*y[i] (exact long
  * accumulator, then one rounding to nearest-even). */
 double oc_dot_exact(int64_t n, const double *x, const double *y);

@@ -94,7 +94,7 @@ class RmParams(C.Structure):
 
 #: every entry point declared in include/bidomain.h
 EXPORTS = (
-    "bd_strerror", "bd_launch_count", "bd_dot_exact", "bd_dot_exact_noalloc",
+    "bd_strerror", "bd_launch_count", "bd_spgemm_path_counts", "bd_dot_exact", "bd_dot_exact_noalloc",
     "amg_options_default", "solve_options_default", "bd_rm_params_default",
     "bd_assemble", "bd_system_info", "bd_system_export", "bd_system_destroy",
     "amg_setup", "amg_setup_from_csr", "amg_num_levels", "amg_level_info", "amg_level_lanes",
@@ -130,6 +130,7 @@ def lib():
             L.bd_dot_exact_noalloc.argtypes = [_vp, _vp, C.c_longlong, _vp, _vp]
             L.bd_launch_count.argtypes = []
             L.bd_launch_count.restype = C.c_longlong
+            L.bd_spgemm_path_counts.argtypes = [_P(C.c_longlong), _P(C.c_longlong)]
             L.amg_options_default.argtypes = [_P(AmgOptions)]
             L.amg_options_default.restype = None
             L.solve_options_default.argtypes = [_P(SolveOptions)]
@@ -195,6 +196,13 @@ def lib():
 
 def bd_launch_count() -> int:
     return lib().bd_launch_count()
+
+
+def bd_spgemm_path_counts() -> tuple:
+    """(hash-path calls, dense-path calls) of the setup's SpGEMM so far."""
+    a, b = C.c_longlong(0), C.c_longlong(0)
+    _check(lib().bd_spgemm_path_counts(C.byref(a), C.byref(b)), "bd_spgemm_path_counts")
+    return a.value, b.value
 
 
 def strerror(status: int) -> str:

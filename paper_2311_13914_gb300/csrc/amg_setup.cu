@@ -409,6 +409,7 @@ static int spgemm(int nrows, int ncols, const int *arp, const int *aci, const do
         if (mub <= kHashProducts) dense = false;
     }
     int HCn = 0, warps_n = 1;
+    ::bd::note_spgemm_path(dense);
     if (dense) {
         BD_TRY(mark.alloc((size_t)grid * ncols));
         BD_TRY(acc.alloc((size_t)grid * ncols * BB));

@@ -18,6 +18,10 @@ namespace bd {
 // reports the running total (host-side, atomic).
 void note_launch();
 void note_launches(long long n);  // adds n (may be negative: undo capture-time counts)
+// SpGEMM calls of the setup by path (hash: warp per row; dense: block per row),
+// counted process-wide for bd_spgemm_path_counts().
+void note_spgemm_path(bool dense);
+long long spgemm_path_count(bool dense);
 long long launch_count();
 
 // ------------------------------------------------------------------ errors

@@ -16,6 +16,9 @@ static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+static std::atomic<long long> g_spgemm_paths[2]{{0}, {0}};
+void note_spgemm_path(bool dense) { g_spgemm_paths[dense ? 1 : 0].fetch_add(1, std::memory_order_relaxed); }
+long long spgemm_path_count(bool dense) { return g_spgemm_paths[dense ? 1 : 0].load(std::memory_order_relaxed); }
 
 void record_cuda_error(cudaError_t e, const char *what, const char *file, int line)
 {
@@ -494,6 +497,14 @@ extern "C" const char *bd_strerror(int st)
 }
 
 extern "C" long long bd_launch_count(void) { return bd::g_launches.load(); }
+
+extern "C" int bd_spgemm_path_counts(long long *hash_calls, long long *dense_calls)
+{
+    if (!hash_calls || !dense_calls) return BD_EINVAL;
+    *hash_calls = bd::spgemm_path_count(false);
+    *dense_calls = bd::spgemm_path_count(true);
+    return BD_OK;
+}
 
 extern "C" int bd_dot_exact(const double *x, const double *y, long long n, int on_device,
                             double *out, void *stream)

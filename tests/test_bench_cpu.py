@@ -41,3 +41,17 @@ def test_recorded_traffic_only_for_unchanged_sources(monkeypatch):
     assert bench.recorded_traffic(True) == float(kv["traffic_bytes_per_launch_fp32"])
     monkeypatch.setattr(bench, "source_digest", lambda: "0" * 16)
     assert bench.recorded_traffic() is None and bench.recorded_traffic(True) is None
+
+
+def test_cpu_record_whole_simulation_rate_and_one_core_figure(monkeypatch):
+    monkeypatch.setattr(bench, "cpu_model", lambda: "test-cpu")
+    r = {"t_setup": 10.0, "t_step": 0.5, "t_step_one_core": 4.0, "iters": [17, 18],
+         "threads": 16, "warm": 5, "timed": 20, "one_core_steps": 1}
+    c = bench.cpu_record(r, 100)
+    assert c["value"] == pytest.approx(100 / (10.0 + 100 * 0.5))
+    assert c["cores"] == 16 and c["kind"] == "oracle" and c["cpu_model"] == "test-cpu"
+    assert c["one_core"]["value"] == pytest.approx(100 / (10.0 + 100 * 4.0))
+    assert c["solve_phase_solves_per_s"] == pytest.approx(2.0)
+    assert "time steps 5..24" in c["sample"]
+    r["t_step_one_core"] = None
+    assert bench.cpu_record(r, 100)["one_core"] is None

@@ -399,3 +399,34 @@ def test_space_clamped_step_is_explicit_euler(oracle_lib):
         assert np.allclose(w, wn, rtol=1e-15)
         assert np.allclose(v, vn, rtol=1e-9, atol=1e-9 * max(1.0, abs(vn)))
         assert np.abs(ue).max() <= 1e-9 * max(1.0, abs(vn))
+
+
+def test_threaded_solve_phase_is_bitwise_serial(oracle_lib):
+    """The oracle's solve phase runs its independent loops on several threads
+    and every reduction serially: V-cycle, PCG and time step give the same
+    bits on one thread and on four."""
+    m = W.mesh(20, 18, 8)
+    p = W.DEFAULT_PARAMS
+    out = oracle_lib.assemble(m, p, W.fibre_table(m, 120.0, 5.0))
+    H = oracle_lib.Hierarchy(out["A"])
+    f = W.rhs(out["A"].shape[0], 3)
+    N = out["M"].size
+    stim = W.stimulus(m)
+    res = []
+    before = oracle_lib.get_threads()
+    try:
+        for t in (1, 4):
+            try:
+                oracle_lib.set_threads(t)
+            except RuntimeError:
+                pytest.skip("oracle built without OpenMP")
+            z = H.vcycle(f)
+            x, info = H.pcg(f)
+            v, ue, w = np.zeros(N), np.zeros(N), np.zeros(N)
+            for _ in range(3):
+                H.bd_step(out["M"], p, stim, v, ue, w)
+            res.append((z, x, info["iters"], v, ue, w))
+    finally:
+        oracle_lib.set_threads(max(before, 1))
+    for a, b in zip(res[0], res[1]):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
