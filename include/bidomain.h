@@ -285,6 +285,41 @@ int amg_batch_solve(amg_batch *b, const double *const *f, double *const *x, cons
                     void *stream, solve_info *info);
 void amg_batch_destroy(amg_batch *b);
 
+/* ---- f2, stacked: one launch per V-cycle step for many hierarchies ----------
+ * The solves of `count` hierarchies advanced together (no counterpart in the
+ * paper, which solves one system per time step; the batching form of the
+ * many-slab workload).  Level l of the stack holds level l of every member
+ * that has one, the members' operators placed block-diagonally, so every
+ * V-cycle step of Algorithm 2 (Chebyshev(2)-Jacobi smoothing of Appendix A,
+ * residual, restriction, the dense coarsest solves, prolongation) is ONE
+ * kernel launch for all members; the projected PCG of Section 2.2 keeps its
+ * scalars (null-space means, alpha, beta, the stopping test on ||r||_2) per
+ * member, each reduced over that member's nodes in a fixed order.  A batch
+ * solve is one CUDA graph whose WHILE loop runs until no member iterates;
+ * members that stop (converged, breakdown, max_it) keep their iterate.  Each
+ * member's result agrees with amg_solve of its hierarchy to rounding (the
+ * stacked reductions sum in another order) and meets the same rtol.
+ * amg_stack_create: h[0..count) distinct hierarchies of one V-cycle precision
+ *   with Chebyshev degree 2; their operators are copied into the stack (the
+ *   hierarchies must outlive it and keep their forms: amg_set_level_lanes
+ *   refuses them with BD_ESTATE while the stack exists).  Synchronises
+ *   `stream`.  Errors: BD_EINVAL, BD_ERANGE (more than 2^30 nodes on a level),
+ *   BD_ENOMEM, BD_ECUDA.
+ * amg_stack_solve: f[k], x[k]: DEVICE pointers to 2 n_k doubles (f_k the
+ *   right-hand side; x_k the initial guess if opts->warm_start, the solution
+ *   on return, with mean-zero u_e).  strict mode is not supported (BD_EINVAL).
+ *   info: NULL or count entries (solve_ms: the whole batch's device time).
+ *   The graph is built on the first call and rebuilt when the pointers change.
+ *   Synchronises `stream`.  Returns BD_OK or the first failing member's status.
+ * amg_stack_info: stack levels and kernel launches per PCG iteration (all
+ *   members together; after the first solve). */
+typedef struct amg_stack amg_stack;
+int amg_stack_create(amg_hierarchy *const *h, int count, void *stream, amg_stack **out);
+int amg_stack_solve(amg_stack *b, const double *const *f, double *const *x, const solve_options *opts,
+                    void *stream, solve_info *info);
+int amg_stack_info(const amg_stack *b, int *levels, long long *launches_per_iteration);
+void amg_stack_destroy(amg_stack *b);
+
 /* ---- live timing of the dominant kernel ------------------------------------
  * When enabled, every application of the finest-level operator (the fused
  * SpMV launches of the V-cycle, and of PCG when the V-cycle is FP64) is

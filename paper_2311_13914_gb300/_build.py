@@ -26,6 +26,7 @@ UNITS = {
     "bd_assemble.cu": ["-fmad=false"],
     "amg_setup.cu": ["-fmad=false"],
     "amg_solve.cu": [],
+    "amg_stack.cu": [],
     "bd_step.cu": [],
     "bd_serve.cu": [],
     "bd_decoupled.cu": [],

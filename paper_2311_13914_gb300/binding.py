@@ -100,7 +100,8 @@ EXPORTS = (
     "amg_setup", "amg_setup_from_csr", "amg_num_levels", "amg_level_info", "amg_level_lanes",
     "amg_set_level_lanes", "amg_export_level",
     "amg_vcycle", "amg_solve", "amg_destroy", "amg_batch_create", "amg_batch_solve",
-    "amg_batch_destroy", "amg_profile_enable", "amg_profile_read", "amg_profile_breakdown",
+    "amg_batch_destroy", "amg_stack_create", "amg_stack_solve", "amg_stack_info", "amg_stack_destroy",
+    "amg_profile_enable", "amg_profile_read", "amg_profile_breakdown",
     "bd_sim_create", "bd_sim_set_state", "bd_sim_get_state", "bd_step", "bd_sim_destroy",
     "bd_elliptic_setup", "bd_dsim_create", "bd_dsim_set_state", "bd_dsim_get_state", "bd_dsim_step",
     "bd_dsim_destroy",
@@ -157,6 +158,11 @@ def lib():
             L.amg_batch_solve.argtypes = [_vp, _P(_vp), _P(_vp), _P(SolveOptions), _vp, _P(SolveInfo)]
             L.amg_batch_destroy.argtypes = [_vp]
             L.amg_batch_destroy.restype = None
+            L.amg_stack_create.argtypes = [_P(_vp), C.c_int, _vp, _P(_vp)]
+            L.amg_stack_solve.argtypes = [_vp, _P(_vp), _P(_vp), _P(SolveOptions), _vp, _P(SolveInfo)]
+            L.amg_stack_info.argtypes = [_vp, _P(C.c_int), _P(C.c_longlong)]
+            L.amg_stack_destroy.argtypes = [_vp]
+            L.amg_stack_destroy.restype = None
             L.amg_profile_enable.argtypes = [_vp, C.c_int]
             L.amg_profile_read.argtypes = [_vp, _P(KernelProfile)]
             L.amg_profile_breakdown.argtypes = [_vp, _P(C.c_double), _P(C.c_longlong)]
@@ -495,6 +501,47 @@ def amg_batch_solve(b: Batch, fs, xs, opts: SolveOptions | None = None, stream=N
     if raise_on_error and st != BD_OK:
         raise BidomainError(st, "amg_batch_solve")
     return [i.as_dict() for i in infos]
+
+
+class Stack(_Handle):
+    _destroy = "amg_stack_destroy"
+
+
+def amg_stack_create(hs, stream=None) -> Stack:
+    """Stack the hierarchies hs level by level: one launch per V-cycle step
+    for all of them (the hierarchies must outlive the stack)."""
+    arr = (_vp * len(hs))(*[h.ptr for h in hs])
+    out = _vp()
+    _check(lib().amg_stack_create(arr, len(hs), _stream(stream), C.byref(out)), "amg_stack_create")
+    return Stack(out, keep=tuple(hs))
+
+
+def amg_stack_solve(b: Stack, fs, xs, opts: SolveOptions | None = None, stream=None,
+                    raise_on_error: bool = True) -> list:
+    """Solve every member system in one graph launch.  fs, xs: CUDA float64
+    tensors (x used in place).  Returns the per-member info dicts."""
+    n = len(fs)
+    if len(xs) != n:
+        raise ValueError("fs and xs differ in length")
+    fp, xp = (_vp * n)(), (_vp * n)()
+    for k in range(n):
+        pf, df, _ = _arr(fs[k], np.float64)
+        px, dx, _ = _arr(xs[k], np.float64)
+        if not (df and dx):
+            raise ValueError("stacked solves take CUDA tensors")
+        fp[k], xp[k] = pf, px
+    o = opts if opts is not None else solve_options_default()
+    infos = (SolveInfo * n)()
+    st = lib().amg_stack_solve(b.ptr, fp, xp, C.byref(o), _stream(stream), infos)
+    if raise_on_error and st != BD_OK:
+        raise BidomainError(st, "amg_stack_solve")
+    return [i.as_dict() for i in infos]
+
+
+def amg_stack_info(b: Stack) -> dict:
+    lv, nl = C.c_int(0), C.c_longlong(0)
+    _check(lib().amg_stack_info(b.ptr, C.byref(lv), C.byref(nl)), "amg_stack_info")
+    return {"levels": lv.value, "launches_per_iteration": nl.value}
 
 
 def amg_profile_enable(h: Hierarchy, enable: int = 1):
