@@ -34,7 +34,7 @@ T_STEPS = 100           # time steps per simulation
 STIM_MS = 1.0           # stimulus duration
 PROFILED_SOLVES = 2     # solves per step timed launch by launch (the rest run as graphs)
 FP64_ALU_PEAK = 152 * 2 * 2 * 2.07e9   # SMs x DFMA/clk/SM x flop/FMA x max SM clock
-FP32_ALU_PEAK = 152 * 128 * 2 * 2.07e9  # SMs x FP32 lanes/SM x flop/FMA x max SM clock
+FP64_OPS_PEAK = 152 * 2 * 2.07e9       # FP64 pipe issue rate: SMs x operations/clk/SM x max SM clock
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fine_operator_traffic.txt")
 
@@ -301,7 +301,7 @@ def run_ours(args):
             record["true_rel_res"].append(info["true_rel_res"])
             if profile:
                 pr = B.amg_profile_read(h)  # sums survive disabling
-                for k in ("launches", "total_ms", "bytes", "flops"):
+                for k in ("launches", "total_ms", "bytes", "flops", "fp64_ops"):
                     record["prof_" + k] += pr[k]
                 record["prof_precision"] = pr["precision"]
             if not record.get("levels"):
@@ -317,7 +317,8 @@ def run_ours(args):
     for _ in range(args.warmup):
         one_step(False, None)
     rec = {"setup_ms": [], "solve_ms": [], "iters": [], "true_rel_res": [], "prof_launches": 0,
-           "prof_total_ms": 0.0, "prof_bytes": 0.0, "prof_flops": 0.0, "prof_precision": 0}
+           "prof_total_ms": 0.0, "prof_bytes": 0.0, "prof_flops": 0.0, "prof_fp64_ops": 0.0,
+           "prof_precision": 0}
     clocks = ClockSampler(local)
     barrier(dist, local)
     torch.cuda.synchronize()
@@ -440,36 +441,42 @@ def run_ours(args):
     peaks = measured_peaks()
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     prof_s = rec["prof_total_ms"] / 1e3
+    nl = max(rec["prof_launches"], 1)
     achieved_gbs = rec["prof_bytes"] / prof_s / 1e9 if prof_s > 0 else None
     achieved_tflops = rec["prof_flops"] / prof_s / 1e12 if prof_s > 0 else None
+    achieved_tops = rec["prof_fp64_ops"] / prof_s / 1e12 if prof_s > 0 else None
     fp32 = rec["prof_precision"] == 1
-    alu_peak = FP32_ALU_PEAK if fp32 else FP64_ALU_PEAK
     t_hbm = rec["prof_bytes"] / (hbm_peak * 1e9)
-    t_alu = rec["prof_flops"] / alu_peak
+    # FP64: every operation the fused launches issue to the FP64 pipe (the 2
+    # FMA per stored node pair and the epilogues), against its issue rate;
+    # the FP32 V-cycle's launches issue almost none
+    t_alu = rec["prof_fp64_ops"] / FP64_OPS_PEAK
     per_launch = rec["prof_bytes"] / rec["prof_launches"] if rec["prof_launches"] else None
     # the recorded figure is for the 128x128x32 workload only
     traffic = recorded_traffic(fp32) if args.workload == "paper" else None
-    # the bound is whichever floor is higher for the flops the kernel executes
-    # (FP64: 2 DFMA per stored node pair in the (v + u, u) form) and the
-    # algorithmic bytes it must move
-    if t_alu > t_hbm:
-        roof = {"bound": "alu", "achieved": achieved_tflops, "peak": alu_peak / 1e12,
-                "unit": "TFLOP/s", "frac": achieved_tflops / (alu_peak / 1e12),
-                "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if fp32 else
-                                "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe)")}
-    else:
-        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved_gbs / hbm_peak,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"}
+    hbm = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+           "frac": achieved_gbs / hbm_peak if achieved_gbs else None,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"}
+    alu = {"bound": "alu", "achieved": achieved_tops, "peak": FP64_OPS_PEAK / 1e12, "unit": "Top/s",
+           "frac": achieved_tops / (FP64_OPS_PEAK / 1e12) if achieved_tops else None,
+           "peak_source": "derived: 152 SMs x 2 FP64 operations/clk x 2.07 GHz (FP64 pipe issue rate; "
+                          "an FMA, add or multiply is one operation)"}
+    # the bound is whichever floor is higher: the algorithmic bytes at the
+    # measured HBM peak, or the FP64 operations at the FP64 pipe's issue rate
+    roof = dict(alu if t_alu > t_hbm else hbm)
     roof.update({"traffic": traffic,
                  "kernel": ("finest-level operator, sliced ELL, FP32 V-cycle (fused epilogues)" if fp32
-                            else "finest-level operator, sliced ELL, FP64 (fused epilogues)"),
+                            else "finest-level operator, sliced ELL, FP64 (fused epilogues) and PCG A p"),
                  "algorithmic_bytes_per_launch": per_launch, "launches": rec["prof_launches"],
-                 "hbm_gbs": achieved_gbs, "hbm_frac": achieved_gbs / hbm_peak if achieved_gbs else None,
-                 "alu_tflops": achieved_tflops, "alu_frac": achieved_tflops / (alu_peak / 1e12),
-                 "floors_us": {"hbm": 1e6 * t_hbm / max(rec["prof_launches"], 1),
-                               "alu": 1e6 * t_alu / max(rec["prof_launches"], 1)},
-                 "mean_launch_us": 1e3 * rec["prof_total_ms"] / max(rec["prof_launches"], 1)})
+                 "fp64_ops_per_launch": rec["prof_fp64_ops"] / nl,
+                 "hbm_gbs": achieved_gbs, "hbm_frac": hbm["frac"],
+                 "fp64_tops": achieved_tops, "fp64_pipe_frac": alu["frac"],
+                 # FMA = 2 flops against the all-FMA FP64 peak (FP64 launches only)
+                 "fp64_tflops": None if fp32 else achieved_tflops,
+                 "fp64_tflops_frac": (achieved_tflops / (FP64_ALU_PEAK / 1e12)
+                                      if achieved_tflops and not fp32 else None),
+                 "floors_us": {"hbm": 1e6 * t_hbm / nl, "fp64_pipe": 1e6 * t_alu / nl},
+                 "mean_launch_us": 1e3 * rec["prof_total_ms"] / nl})
     out = {
         "metric": "AMG-PCG solves/sec to rtol 1e-8 (coupled Bidomain, paper-size slab, time stepping)",
         "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,

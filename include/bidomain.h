@@ -341,6 +341,10 @@ typedef struct {
     double bytes;
     double flops;
     int precision;     /* 0: the timed launches are FP64, 1: FP32 (V-cycle) */
+    double fp64_ops;   /* FP64 pipe operations of those launches: a fused
+                          multiply-add, an add or a multiply counts one (2 FMA
+                          per stored node pair in the (v + u, u) form, and the
+                          fused epilogue's operations per node) */
 } amg_kernel_profile;
 int amg_profile_enable(amg_hierarchy *h, int enable);
 int amg_profile_read(const amg_hierarchy *h, amg_kernel_profile *out);

@@ -70,7 +70,7 @@ class SolveInfo(C.Structure):
 
 class KernelProfile(C.Structure):
     _fields_ = [("launches", C.c_longlong), ("total_ms", C.c_double), ("bytes", C.c_double),
-                ("flops", C.c_double), ("precision", C.c_int)]
+                ("flops", C.c_double), ("precision", C.c_int), ("fp64_ops", C.c_double)]
 
 
 class ServerOptions(C.Structure):

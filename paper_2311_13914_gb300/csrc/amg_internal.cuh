@@ -104,7 +104,7 @@ struct amg_hierarchy {
     // live timing of the finest-level operator applications
     int prof = 0;
     std::vector<cudaEvent_t> ev;      // pairs
-    std::vector<double> ev_bytes, ev_flops;
+    std::vector<double> ev_bytes, ev_flops, ev_ops;
     int ev_used = 0;
     amg_kernel_profile prof_sum{};
     // per-step breakdown (profiling level 2): label of each event pair and the
@@ -143,6 +143,6 @@ enum ProfRole {
     R_COARSE = 15 * 16, R_VIN, R_VOUT, R_ZSTATS, R_PUPDATE, R_AP, R_XRUPDATE
 };
 int prof_begin(amg_hierarchy *h, cudaStream_t s, int label, bool fine);
-void prof_end(amg_hierarchy *h, int slot, double bytes, double flops, cudaStream_t s);
+void prof_end(amg_hierarchy *h, int slot, double bytes, double flops, cudaStream_t s, double ops = 0.0);
 void prof_collect(amg_hierarchy *h);
 }  // namespace bd

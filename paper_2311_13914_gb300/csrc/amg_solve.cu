@@ -627,6 +627,7 @@ int prof_begin(amg_hierarchy *h, cudaStream_t s, int label, bool fine)
             if (h->ev.size() % 2 == 0) {
                 h->ev_bytes.push_back(0.0);
                 h->ev_flops.push_back(0.0);
+                h->ev_ops.push_back(0.0);
                 h->ev_label.push_back(-1);
             }
         }
@@ -634,18 +635,20 @@ int prof_begin(amg_hierarchy *h, cudaStream_t s, int label, bool fine)
     int slot = h->ev_used++;
     h->ev_bytes[slot] = 0.0;
     h->ev_flops[slot] = 0.0;
+    h->ev_ops[slot] = 0.0;
     h->ev_label[slot] = label;
     cudaEventRecord(h->ev[2 * slot], s);
     return slot;
 }
 
 // bytes/flops > 0 mark a finest-operator application (amg_kernel_profile sums)
-void prof_end(amg_hierarchy *h, int slot, double bytes, double flops, cudaStream_t s)
+void prof_end(amg_hierarchy *h, int slot, double bytes, double flops, cudaStream_t s, double ops)
 {
     if (slot < 0) return;
     cudaEventRecord(h->ev[2 * slot + 1], s);
     h->ev_bytes[slot] = bytes;
     h->ev_flops[slot] = flops;
+    h->ev_ops[slot] = ops;
 }
 
 void prof_collect(amg_hierarchy *h)
@@ -659,6 +662,7 @@ void prof_collect(amg_hierarchy *h)
             h->prof_sum.total_ms += ms;
             h->prof_sum.bytes += h->ev_bytes[i];
             h->prof_sum.flops += h->ev_flops[i];
+            h->prof_sum.fp64_ops += h->ev_ops[i];
         }
         const int lab = h->ev_label[i];
         if (h->prof >= 2 && lab >= 0 && lab < 256) {
@@ -691,6 +695,24 @@ static double fine_flops(const amg_hierarchy *h, const Level &L, bool su)
 {
     if (h->sell.valid) return (su ? 4.0 : 5.0) * 32.0 * (double)h->sell.slots;
     return 8.0 * (double)L.A.nb;
+}
+// FP64 pipe operations (a fused multiply-add, an add and a multiply count one
+// each: what the pipe issues) of one finest-level launch of the FP64 V-cycle
+// or of the PCG's A p: per stored slot the 2 FMA of the (v + u, u) form, per
+// node the row tail (c M v + a, a + b, and v = (v + u) - u) and the fused
+// step as written in its epilogue: pre-smoother 12, residual 2, first
+// post-smoothing half 9, second half 12 (17 with the PCG's z statistics),
+// A p with p.Ap 3.  The FP32 V-cycle's launches issue FP64 operations only
+// for the z statistics (conversions and sums, 10 per node).  Block-CSR finest
+// levels: 4 FMA per 2x2 block, epilogues not counted.
+enum FineRole { FR_PRE, FR_RESID, FR_POST1, FR_POST2, FR_POST2Z, FR_AP };
+template <class S>
+static double fine_ops(const amg_hierarchy *h, const Level &L, int role)
+{
+    if (!h->sell.valid) return sizeof(S) == 8 || role == FR_AP ? 4.0 * (double)L.A.nb : 0.0;
+    if (sizeof(S) == 4 && role != FR_AP) return role == FR_POST2Z ? 10.0 * L.N : 0.0;
+    static const double epi[] = {12.0, 2.0, 9.0, 12.0, 17.0, 3.0};
+    return 2.0 * 32.0 * (double)h->sell.slots + (3.0 + epi[role]) * (double)L.N;
 }
 
 // ------------------------------------------------------------------ coarsest level
@@ -840,7 +862,7 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
             int sl = prof_begin(h, s, 16 * l + R_PRE, l == 0);
             BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{d0},
                                    EpiPre<S, SU>{f, lv.invd, d0, u, (S)L.ch_c1, (S)L.ch_c2}, s));
-            prof_end(h, sl, l == 0 ? fine_bytes<S>(h, L, 4) : 0.0, fine_flops(h, L, SU), s);
+            prof_end(h, sl, l == 0 ? fine_bytes<S>(h, L, 4) : 0.0, fine_flops(h, L, SU), s, fine_ops<S>(h, L, FR_PRE));
         } else {
             int sl = prof_begin(h, s, 16 * l + R_PRE, false);
             k_copy2<S><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, d0, u); ::bd::note_launch();
@@ -849,7 +871,7 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
         }
         int sr = prof_begin(h, s, 16 * l + R_RESID, l == 0);
         BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{u}, EpiResid<S>{f, lv.r}, s));
-        prof_end(h, sr, l == 0 ? fine_bytes<S>(h, L, 3) : 0.0, fine_flops(h, L, SU), s);
+        prof_end(h, sr, l == 0 ? fine_bytes<S>(h, L, 3) : 0.0, fine_flops(h, L, SU), s, fine_ops<S>(h, L, FR_RESID));
         const Level &C = h->lev[l + 1];
         const LV<S> cv = view<S>(h, l + 1);
         int sx = prof_begin(h, s, 16 * l + R_RESTRICT, false);
@@ -872,7 +894,7 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
         int s1 = prof_begin(h, s, 16 * l + R_POST1, l == 0);
         BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{u},
                                EpiPost1<S, SU>{f, lv.invd, u, lv.r, lv.d, lv.w, (S)L.ch_inv_theta}, s));
-        prof_end(h, s1, l == 0 ? fine_bytes<S>(h, L, 6) : 0.0, fine_flops(h, L, SU), s);
+        prof_end(h, s1, l == 0 ? fine_bytes<S>(h, L, 6) : 0.0, fine_flops(h, L, SU), s, fine_ops<S>(h, L, FR_POST1));
         if (deg2) {
             int s2 = prof_begin(h, s, 16 * l + R_POST2, l == 0);
             const EpiPost2<S, SU> epi{lv.r, lv.d, lv.invd, lv.w, u, (S)L.ch_c1, (S)L.ch_c2};
@@ -885,7 +907,8 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
             } else {
                 BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{lv.d}, epi, s));
             }
-            prof_end(h, s2, bytes, fine_flops(h, L, SU), s);
+            prof_end(h, s2, bytes, fine_flops(h, L, SU), s,
+                     fine_ops<S>(h, L, (l == 0 && zo && h->sell.valid) ? FR_POST2Z : FR_POST2));
         } else {
             int s2 = prof_begin(h, s, 16 * l + R_POST2, false);
             k_copy2<S><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, lv.w, u); ::bd::note_launch();
@@ -1345,8 +1368,12 @@ struct ZOut {
 };
 
 // FP64: at most 64 registers (4 blocks per SM, as the other FP64 finest-level
-// kernels); FP32: the FP64 sums need more than the 32 registers of 8 blocks
-// per SM, so 6.
+// kernels).  FP32 V-cycle: the per-thread partial sums are FP32, the
+// precision z itself comes in (the V-cycle's output, converted exactly), with
+// r and z_old rounded to FP32 for the products; blocks and the grid add the
+// partials in FP64.  That keeps the kernel within 32 registers, so it runs 8
+// blocks per SM like the other FP32 finest-level kernels, which need every
+// resident warp to keep enough bytes in flight.
 template <class S, bool SU, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_sell_z(int N, const int *__restrict__ sptr,
                                                     const int *__restrict__ col,
@@ -1356,7 +1383,7 @@ __global__ void __launch_bounds__(256, MINB) k_sell_z(int N, const int *__restri
 {
     __shared__ int off[27];
     if (sizeof(S) == 4) stage_stencil(st, off);
-    double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+    S a = 0, b = 0, c = 0, d = 0;
     const int lane = threadIdx.x & 31, e = share_hi(N);
     for (int p = share_lo(N) + threadIdx.x; p < e; p += blockDim.x) {
         S y0, y1;
@@ -1365,15 +1392,16 @@ __global__ void __launch_bounds__(256, MINB) k_sell_z(int N, const int *__restri
         const v2<S> u = epi.value(p, y0, y1);
         const double2 z = make_double2((double)u.x, (double)u.y), r = zo.r[p];
         zo.z[p] = z;
-        a += z.y;
-        b += r.y;
-        c += r.x * z.x + r.y * z.y;
+        const S rx = (S)r.x, ry = (S)r.y;
+        a += u.y;
+        b += ry;
+        c += rx * u.x + ry * u.y;
         if (zo.zold) {
             const double2 o = zo.zold[p];
-            d += r.x * o.x + r.y * o.y;
+            d += rx * (S)o.x + ry * (S)o.y;
         }
     }
-    block_finish<4, 256>(a, b, c, d, zo.fin);
+    block_finish<4, 256>((double)a, (double)b, (double)c, (double)d, zo.fin);
 }
 
 static int zo_streams(const ZOut *zo) { return zo->zold ? 3 : 2; }
@@ -1384,7 +1412,7 @@ static int launch_sell_z(amg_hierarchy *h, const LV<S> &lv, const EpiPost2<S, SU
 {
     const FineSell &F = h->sell;
     const int N = h->lev[0].N;
-    constexpr int MB = sizeof(S) == 8 ? 4 : 6;
+    constexpr int MB = sizeof(S) == 8 ? 4 : 8;
     const int grid = (int)std::min<long long>(((long long)N + 31) / 32, (long long)kSM * MB);
     k_sell_z<S, SU, MB><<<grid, 256, 0, s>>>(N, F.sptr.p, F.col.p, F.code.p, stencil_of(F), lv.kk, lv.cm,
                                              GatherVec<S>{lv.d}, epi, zo);
@@ -1756,7 +1784,8 @@ static int pcg_solve_loop(amg_hierarchy *h, const double *f_dev, double *x_dev, 
             // when the V-cycle is FP64 too (one kernel family per profile)
             int sq = prof_begin(h, s, R_AP, !h->prec32);
             fine_reduce<0>(h, p, nullptr, q, make_fin(h, 4, 0), s);
-            prof_end(h, sq, h->prec32 ? 0.0 : fine_bytes<double>(h, L0, 2), fine_flops(h, L0, true), s);
+            prof_end(h, sq, h->prec32 ? 0.0 : fine_bytes<double>(h, L0, 2), fine_flops(h, L0, true), s,
+                     fine_ops<double>(h, L0, FR_AP));
             int sx = prof_begin(h, s, R_XRUPDATE, false);
             xr_update(h, N, x, r, p, q, make_fin(h, 2, 0), s, d0);
             prof_end(h, sx, 0.0, 0.0, s);

@@ -83,3 +83,6 @@ def test_struct_layouts_match_header(L):
     assert C.sizeof(L.AmgOptions) == 8 + 5 * 4 + 4 + 2 * 8 + 8 + 4 + 4
     assert C.sizeof(L.SolveOptions) == 8 + 3 * 4 + 4
     assert C.sizeof(L.SolveInfo) == 2 * 4 + 3 * 8 + 8
+    assert C.sizeof(L.KernelProfile) == 8 + 3 * 8 + 4 + 4 + 8
+    assert [f for f, _ in L.KernelProfile._fields_] == ["launches", "total_ms", "bytes", "flops",
+                                                        "precision", "fp64_ops"]
