@@ -232,38 +232,55 @@ __global__ void k_spgemm_bound(int nrows, const int *__restrict__ arp, const int
     ub[i] = u > INT_MAX ? INT_MAX : (int)u;
 }
 
+// Hash-path SpGEMM: L lanes per output row, 32/L rows per warp (L from the
+// average row length of B, so that short rows of B -- a tentative
+// prolongator has one block per row -- do not leave most lanes idle: every
+// FP64 instruction costs the pipe a full warp slot however few lanes are on).
+// Each row has its own hash table in shared memory.
+template <int L>
+__device__ __forceinline__ unsigned sub_mask(int lane)
+{
+    return L == 32 ? 0xffffffffu : (((1u << L) - 1u) << (lane & ~(L - 1)));
+}
+
+template <int L>
 __global__ void k_spgemm_count_hash(int nrows, const int *__restrict__ arp, const int *__restrict__ aci,
                                     const int *__restrict__ brp, const int *__restrict__ bci, int HC,
                                     int *__restrict__ cnt, int *overflow)
 {
+    constexpr int R = 32 / L;
     extern __shared__ int hk[];
-    int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int *keys = hk + (size_t)wid * HC;
-    for (int i = blockIdx.x * warps + wid; i < nrows; i += gridDim.x * warps) {
-        for (int x = lane; x < HC; x += 32) keys[x] = -1;
+    const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sub = lane / L, sl = lane % L;
+    int *keys = hk + ((size_t)wid * R + sub) * HC;
+    for (int base = (blockIdx.x * warps + wid) * R; base < nrows; base += gridDim.x * warps * R) {
+        const int i = base + sub;
+        for (int x = sl; x < HC; x += L) keys[x] = -1;
         __syncwarp();
         int c = 0;
-        for (int t = arp[i]; t < arp[i + 1]; t++) {
-            int k = aci[t];
-            for (int s2 = brp[k] + lane; s2 < brp[k + 1]; s2 += 32) {
-                int j = bci[s2], h = hslot(j, HC - 1), probe = 0;
-                for (; probe < HC; probe++) {
-                    int old = atomicCAS(&keys[h], -1, j);
-                    if (old == -1) { c++; break; }
-                    if (old == j) break;
-                    h = (h + 1) & (HC - 1);
+        if (i < nrows) {
+            for (int t = arp[i]; t < arp[i + 1]; t++) {
+                int k = aci[t];
+                for (int s2 = brp[k] + sl; s2 < brp[k + 1]; s2 += L) {
+                    int j = bci[s2], h = hslot(j, HC - 1), probe = 0;
+                    for (; probe < HC; probe++) {
+                        int old = atomicCAS(&keys[h], -1, j);
+                        if (old == -1) { c++; break; }
+                        if (old == j) break;
+                        h = (h + 1) & (HC - 1);
+                    }
+                    if (probe == HC) atomicOr(overflow, 1);
                 }
-                if (probe == HC) atomicOr(overflow, 1);
             }
         }
 #pragma unroll
-        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if (lane == 0) cnt[i] = c;
+        for (int o = L / 2; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o, L);
+        if (i < nrows && sl == 0) cnt[i] = c;
         __syncwarp();
     }
 }
 
-template <int BS>
+template <int BS, int L>
 __global__ void k_spgemm_fill_hash(int nrows, const int *__restrict__ arp, const int *__restrict__ aci,
                                    const double *__restrict__ av, const int *__restrict__ brp,
                                    const int *__restrict__ bci, const double *__restrict__ bv, int HC,
@@ -271,57 +288,71 @@ __global__ void k_spgemm_fill_hash(int nrows, const int *__restrict__ arp, const
                                    double *__restrict__ cv)
 {
     constexpr int BB = BS * BS;
+    constexpr int R = 32 / L;
     extern __shared__ double hs[];
-    int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    size_t per = (size_t)HC * BB + (size_t)(3 * HC + 1) / 2;  // in doubles
-    double *acc = hs + (size_t)wid * per;
+    const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sub = lane / L, sl = lane % L;
+    const size_t per = (size_t)HC * BB + (size_t)(3 * HC + 1) / 2;  // in doubles
+    double *acc = hs + ((size_t)wid * R + sub) * per;
     int *keys = (int *)(acc + (size_t)HC * BB);
     int *sk = keys + HC, *sp = sk + HC;
-    for (int i = blockIdx.x * warps + wid; i < nrows; i += gridDim.x * warps) {
-        for (int x = lane; x < HC; x += 32) keys[x] = -1;
+    for (int base = (blockIdx.x * warps + wid) * R; base < nrows; base += gridDim.x * warps * R) {
+        const int i = base + sub;
+        const bool act = i < nrows;
+        for (int x = sl; x < HC; x += L) keys[x] = -1;
         __syncwarp();
-        for (int t = arp[i]; t < arp[i + 1]; t++) {
-            int k = aci[t];
-            double a[BB];
+        // middle indices in ascending order, all rows of the warp in step (a
+        // barrier per middle index keeps each entry's additions in that order)
+        const int t0 = act ? arp[i] : 0, tn = act ? arp[i + 1] - t0 : 0;
+        int tmax = tn;
 #pragma unroll
-            for (int e = 0; e < BB; e++) a[e] = av[(size_t)t * BB + e];
-            for (int s2 = brp[k] + lane; s2 < brp[k + 1]; s2 += 32) {
-                int j = bci[s2], h = hslot(j, HC - 1);
-                for (int probe = 0; probe < HC; probe++) {
-                    int old = atomicCAS(&keys[h], -1, j);
-                    if (old == -1) {
+        for (int o = 16; o; o >>= 1) tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+        for (int tt = 0; tt < tmax; tt++) {
+            if (tt < tn) {
+                const int t = t0 + tt;
+                const int k = aci[t];
+                double a[BB];
 #pragma unroll
-                        for (int e = 0; e < BB; e++) acc[(size_t)h * BB + e] = 0.0;
-                        break;
+                for (int e = 0; e < BB; e++) a[e] = av[(size_t)t * BB + e];
+                for (int s2 = brp[k] + sl; s2 < brp[k + 1]; s2 += L) {
+                    int j = bci[s2], h = hslot(j, HC - 1);
+                    for (int probe = 0; probe < HC; probe++) {
+                        int old = atomicCAS(&keys[h], -1, j);
+                        if (old == -1) {
+#pragma unroll
+                            for (int e = 0; e < BB; e++) acc[(size_t)h * BB + e] = 0.0;
+                            break;
+                        }
+                        if (old == j) break;
+                        h = (h + 1) & (HC - 1);
                     }
-                    if (old == j) break;
-                    h = (h + 1) & (HC - 1);
-                }
-                double *c = acc + (size_t)h * BB;
-                const double *b = bv + (size_t)s2 * BB;
-                if (BS == 1) {
-                    c[0] = c[0] + a[0] * b[0];
-                } else {
-                    c[0] = c[0] + a[0] * b[0];
-                    c[0] = c[0] + a[1] * b[2];
-                    c[1] = c[1] + a[0] * b[1];
-                    c[1] = c[1] + a[1] * b[3];
-                    c[2] = c[2] + a[2] * b[0];
-                    c[2] = c[2] + a[3] * b[2];
-                    c[3] = c[3] + a[2] * b[1];
-                    c[3] = c[3] + a[3] * b[3];
+                    double *c = acc + (size_t)h * BB;
+                    const double *b = bv + (size_t)s2 * BB;
+                    if (BS == 1) {
+                        c[0] = c[0] + a[0] * b[0];
+                    } else {
+                        c[0] = c[0] + a[0] * b[0];
+                        c[0] = c[0] + a[1] * b[2];
+                        c[1] = c[1] + a[0] * b[1];
+                        c[1] = c[1] + a[1] * b[3];
+                        c[2] = c[2] + a[2] * b[0];
+                        c[2] = c[2] + a[3] * b[2];
+                        c[3] = c[3] + a[2] * b[1];
+                        c[3] = c[3] + a[3] * b[3];
+                    }
                 }
             }
             __syncwarp();
         }
         // compact the occupied slots, sort them by column, emit
+        const unsigned smask = sub_mask<L>(lane);
         int n = 0;
-        for (int base = 0; base < HC; base += 32) {
-            int x = base + lane;
-            bool has = keys[x] != -1;
-            unsigned m = __ballot_sync(0xffffffffu, has);
+        for (int x0 = 0; x0 < HC; x0 += L) {
+            const int x = x0 + sl;
+            const bool has = keys[x] != -1;
+            const unsigned m = __ballot_sync(0xffffffffu, has) & smask;
             if (has) {
-                int pos = n + __popc(m & ((1u << lane) - 1u));
+                const int pos = n + __popc(m & ((1u << lane) - 1u));
                 sk[pos] = keys[x];
                 sp[pos] = x;
             }
@@ -329,14 +360,17 @@ __global__ void k_spgemm_fill_hash(int nrows, const int *__restrict__ arp, const
         }
         int p2 = 1;
         while (p2 < n) p2 <<= 1;
-        for (int x = n + lane; x < p2; x += 32) {
+        int p2max = p2;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) p2max = max(p2max, __shfl_xor_sync(0xffffffffu, p2max, o));
+        for (int x = n + sl; x < p2max; x += L) {
             sk[x] = INT_MAX;
             sp[x] = 0;
         }
         __syncwarp();
-        for (int kk = 2; kk <= p2; kk <<= 1)
+        for (int kk = 2; kk <= p2max; kk <<= 1)
             for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-                for (int x = lane; x < p2; x += 32) {
+                for (int x = sl; x < p2max; x += L) {
                     int y = x ^ jj;
                     if (y > x) {
                         bool up = (x & kk) == 0;
@@ -352,11 +386,13 @@ __global__ void k_spgemm_fill_hash(int nrows, const int *__restrict__ arp, const
                 }
                 __syncwarp();
             }
-        int base = crp[i];
-        for (int x = lane; x < n; x += 32) {
-            cci[base + x] = sk[x];
+        if (act) {
+            const int cb = crp[i];
+            for (int x = sl; x < n; x += L) {
+                cci[cb + x] = sk[x];
 #pragma unroll
-            for (int e = 0; e < BB; e++) cv[(size_t)(base + x) * BB + e] = acc[(size_t)sp[x] * BB + e];
+                for (int e = 0; e < BB; e++) cv[(size_t)(cb + x) * BB + e] = acc[(size_t)sp[x] * BB + e];
+            }
         }
         __syncwarp();
     }
@@ -371,10 +407,56 @@ static int pow2_at_least(long long v)
 
 constexpr long long kHashProducts = 4096;  // products per row up to which the hash path is used
 
+// Lanes per output row of the hash path: the power of two nearest above the
+// average row length of B (at most 32).
+static int hash_lanes(double b_per_row)
+{
+    int L = 1;
+    while (L < 32 && L < b_per_row) L <<= 1;
+    return L;
+}
+
+template <int L>
+static int launch_count_hash(int nrows, int HCs, const int *arp, const int *aci, const int *brp, const int *bci,
+                             int *cnt, int *flag, cudaStream_t s)
+{
+    constexpr int R = 32 / L;
+    const size_t per_warp = (size_t)R * HCs * 4;
+    const int warps = std::max(1, std::min(8, (int)((192u << 10) / per_warp)));
+    const size_t smem = (size_t)warps * per_warp;
+    if (smem > (227u << 10)) return BD_ERANGE;
+    BD_CUDA(cudaFuncSetAttribute(k_spgemm_count_hash<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const long long rows_per_block = (long long)warps * R;
+    const int gb = (int)std::min<long long>(kSM * 8, std::max<long long>(1, (nrows + rows_per_block - 1) / rows_per_block));
+    k_spgemm_count_hash<L><<<gb, 32 * warps, smem, s>>>(nrows, arp, aci, brp, bci, HCs, cnt, flag); ::bd::note_launch();
+    BD_LAUNCH_CHECK();
+    return BD_OK;
+}
+
+template <int BS, int L>
+static int launch_fill_hash(int nrows, int HCn, const int *arp, const int *aci, const double *av, const int *brp,
+                            const int *bci, const double *bv, const int *crp, int *cci, double *cv, cudaStream_t s)
+{
+    constexpr int R = 32 / L;
+    const size_t per = ((size_t)HCn * BS * BS + (size_t)(3 * HCn + 1) / 2) * sizeof(double);
+    const size_t per_warp = (size_t)R * per;
+    if (per_warp > (200u << 10)) return BD_ERANGE;
+    const int warps = std::max(1, std::min(8, (int)((200u << 10) / per_warp)));
+    const size_t smem = per_warp * warps;
+    BD_CUDA(cudaFuncSetAttribute(k_spgemm_fill_hash<BS, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const long long rows_per_block = (long long)warps * R;
+    const int gb = (int)std::min<long long>(kSM * 8, std::max<long long>(1, (nrows + rows_per_block - 1) / rows_per_block));
+    k_spgemm_fill_hash<BS, L><<<gb, 32 * warps, smem, s>>>(nrows, arp, aci, av, brp, bci, bv, HCn, crp, cci, cv);
+    ::bd::note_launch();
+    BD_LAUNCH_CHECK();
+    return BD_OK;
+}
+
+// b_per_row: average blocks per row of B (sets the lanes per row of the hash path)
 template <int BS>
 static int spgemm(int nrows, int ncols, const int *arp, const int *aci, const double *av,
                   const int *brp, const int *bci, const double *bv, DBuf<int> &crp, DBuf<int> &cci,
-                  DBuf<double> &cv, long long *cnnz, cudaStream_t s)
+                  DBuf<double> &cv, long long *cnnz, cudaStream_t s, double b_per_row)
 {
     constexpr int BB = BS * BS;
     BD_TRY(crp.alloc((size_t)nrows + 1));
@@ -408,7 +490,8 @@ static int spgemm(int nrows, int ncols, const int *arp, const int *aci, const do
         for (int i = 0; i < nrows; i++) mub = std::max<long long>(mub, ub[i]);
         if (mub <= kHashProducts) dense = false;
     }
-    int HCn = 0, warps_n = 1;
+    int HCn = 0;
+    const int lanes = hash_lanes(b_per_row);
     ::bd::note_spgemm_path(dense);
     if (dense) {
         BD_TRY(mark.alloc((size_t)grid * ncols));
@@ -419,12 +502,17 @@ static int spgemm(int nrows, int ncols, const int *arp, const int *aci, const do
     } else {
         int HCs = pow2_at_least(2 * std::min<long long>(mub, kMaxSortSeg));
         if (HCs < 32) HCs = 32;
-        int warps = std::max(1, std::min(8, (int)((192 << 10) / ((size_t)HCs * 4))));
-        size_t smem = (size_t)warps * HCs * 4;
-        BD_CUDA(cudaFuncSetAttribute(k_spgemm_count_hash, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int gb = std::min(kSM * 8, std::max(1, (nrows + warps - 1) / warps));
-        k_spgemm_count_hash<<<gb, 32 * warps, smem, s>>>(nrows, arp, aci, brp, bci, HCs, cnt.p, flag.p); ::bd::note_launch();
-        BD_LAUNCH_CHECK();
+        // rows whose tables do not fit 32/lanes to a warp take more lanes each
+        int Lc = lanes;
+        while (Lc < 32 && (size_t)(32 / Lc) * HCs * 4 > (192u << 10)) Lc <<= 1;
+        switch (Lc) {
+        case 1: BD_TRY(launch_count_hash<1>(nrows, HCs, arp, aci, brp, bci, cnt.p, flag.p, s)); break;
+        case 2: BD_TRY(launch_count_hash<2>(nrows, HCs, arp, aci, brp, bci, cnt.p, flag.p, s)); break;
+        case 4: BD_TRY(launch_count_hash<4>(nrows, HCs, arp, aci, brp, bci, cnt.p, flag.p, s)); break;
+        case 8: BD_TRY(launch_count_hash<8>(nrows, HCs, arp, aci, brp, bci, cnt.p, flag.p, s)); break;
+        case 16: BD_TRY(launch_count_hash<16>(nrows, HCs, arp, aci, brp, bci, cnt.p, flag.p, s)); break;
+        default: BD_TRY(launch_count_hash<32>(nrows, HCs, arp, aci, brp, bci, cnt.p, flag.p, s)); break;
+        }
     }
     long long total = 0;
     BD_TRY(exclusive_scan(cnt.p, crp.p, nrows, &total, s));
@@ -450,16 +538,19 @@ static int spgemm(int nrows, int ncols, const int *arp, const int *aci, const do
         BD_LAUNCH_CHECK();
     } else {
         HCn = pow2_at_least(2LL * std::max(maxrow, 16));
-        size_t per = ((size_t)HCn * BB + (size_t)(3 * HCn + 1) / 2) * sizeof(double);
-        if (per > (200u << 10)) return BD_ERANGE;
-        warps_n = std::max(1, std::min(8, (int)((200u << 10) / per)));
-        size_t smem = per * warps_n;
-        BD_CUDA(cudaFuncSetAttribute(k_spgemm_fill_hash<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-        int gb = std::min(kSM * 8, std::max(1, (nrows + warps_n - 1) / warps_n));
-        k_spgemm_fill_hash<BS><<<gb, 32 * warps_n, smem, s>>>(nrows, arp, aci, av, brp, bci, bv, HCn,
-                                                              crp.p, cci.p, cv.p); ::bd::note_launch();
-        BD_LAUNCH_CHECK();
+        // rows whose tables do not fit 32/lanes to a warp take more lanes each
+        int Lf = lanes;
+        while (Lf < 32 && (size_t)(32 / Lf) * (((size_t)HCn * BB + (size_t)(3 * HCn + 1) / 2) * sizeof(double)) >
+                              (200u << 10))
+            Lf <<= 1;
+        switch (Lf) {
+        case 1: BD_TRY((launch_fill_hash<BS, 1>(nrows, HCn, arp, aci, av, brp, bci, bv, crp.p, cci.p, cv.p, s))); break;
+        case 2: BD_TRY((launch_fill_hash<BS, 2>(nrows, HCn, arp, aci, av, brp, bci, bv, crp.p, cci.p, cv.p, s))); break;
+        case 4: BD_TRY((launch_fill_hash<BS, 4>(nrows, HCn, arp, aci, av, brp, bci, bv, crp.p, cci.p, cv.p, s))); break;
+        case 8: BD_TRY((launch_fill_hash<BS, 8>(nrows, HCn, arp, aci, av, brp, bci, bv, crp.p, cci.p, cv.p, s))); break;
+        case 16: BD_TRY((launch_fill_hash<BS, 16>(nrows, HCn, arp, aci, av, brp, bci, bv, crp.p, cci.p, cv.p, s))); break;
+        default: BD_TRY((launch_fill_hash<BS, 32>(nrows, HCn, arp, aci, av, brp, bci, bv, crp.p, cci.p, cv.p, s))); break;
+        }
     }
     *cnnz = total;
     return BD_OK;
@@ -974,9 +1065,12 @@ __global__ void k_gj_pivot(int n, int K, int bb, const double *__restrict__ A, d
     for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) D[e / bb][e % bb] = A[(size_t)(K + e / bb) * n + K + e % bb];
     __syncthreads();
     for (int k = 0; k < bb; k++) {
-        const double piv = D[k][k];
+        // one division per pivot: the pivot row is scaled by its reciprocal
+        // (FP64 division is a long sequence on the FP64 pipe, and one thread
+        // block does all of this)
+        const double piv = D[k][k], rpiv = 1.0 / piv;
         if (threadIdx.x < bb) {
-            prow[threadIdx.x] = D[k][threadIdx.x];
+            prow[threadIdx.x] = D[k][threadIdx.x] * rpiv;
             pcol[threadIdx.x] = D[threadIdx.x][k];
         }
         __syncthreads();
@@ -984,10 +1078,10 @@ __global__ void k_gj_pivot(int n, int K, int bb, const double *__restrict__ A, d
         for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) {
             const int i = e / bb, j = e % bb;
             double a;
-            if (i == k && j == k) a = 1.0 / piv;
-            else if (i == k) a = prow[j] / piv;
-            else if (j == k) a = -pcol[i] / piv;
-            else a = D[i][j] - pcol[i] / piv * prow[j];
+            if (i == k && j == k) a = rpiv;
+            else if (i == k) a = prow[j];
+            else if (j == k) a = -pcol[i] * rpiv;
+            else a = D[i][j] - pcol[i] * prow[j];
             D[i][j] = a;
         }
         __syncthreads();
@@ -1125,7 +1219,8 @@ static int coarsen_level(amg_hierarchy *h, int l, bool &is_coarsest, cudaStream_
         k_insert_diag<<<nblk(N + 1), 256, 0, s>>>(N, S.rp.p, S.ci.p, S.v.p, W.rp.p, W.ci.p, W.v.p); ::bd::note_launch();
         BD_LAUNCH_CHECK();
         long long qn = 0;
-        BD_TRY(spgemm<1>(N, N, W.rp.p, W.ci.p, W.v.p, W.rp.p, W.ci.p, W.v.p, Q.rp, Q.ci, Q.v, &qn, s));
+        BD_TRY(spgemm<1>(N, N, W.rp.p, W.ci.p, W.v.p, W.rp.p, W.ci.p, W.v.p, Q.rp, Q.ci, Q.v, &qn, s,
+                         (double)(snnz + N) / std::max(N, 1)));
         BD_TRY(S2.rp.alloc((size_t)N + 1));
         BD_TRY(S2.ci.alloc((size_t)(qn - N)));
         BD_TRY(S2.v.alloc((size_t)(qn - N)));
@@ -1258,7 +1353,7 @@ static int coarsen_level(amg_hierarchy *h, int l, bool &is_coarsest, cudaStream_
     L.P.nbr = N;
     L.P.nbc = Nc;
     BD_TRY(spgemm<2>(N, Nc, L.A.rp.p, L.A.ci.p, L.A.v.p, Pt.rp.p, Pt.ci.p, Pt.v.p, L.P.rp, L.P.ci,
-                     L.P.v, &pnb, s));
+                     L.P.v, &pnb, s, 1.0));  // one block per row of the tentative prolongator
     L.P.nb = pnb;
     k_smooth_p<<<nblk(N), 256, 0, s>>>(N, L.P.rp.p, L.P.ci.p, L.P.v.p, L.agg.p, ptd.p, diag.p, lst.p); ::bd::note_launch();
     BD_LAUNCH_CHECK();
@@ -1268,14 +1363,14 @@ static int coarsen_level(amg_hierarchy *h, int l, bool &is_coarsest, cudaStream_
     BSR AP;
     long long apnb = 0;
     BD_TRY(spgemm<2>(N, Nc, L.A.rp.p, L.A.ci.p, L.A.v.p, L.P.rp.p, L.P.ci.p, L.P.v.p, AP.rp, AP.ci,
-                     AP.v, &apnb, s));
+                     AP.v, &apnb, s, (double)L.P.nb / std::max(N, 1)));
     AP.nbr = N;
     AP.nbc = Nc;
     AP.nb = apnb;
     long long cnb = 0;
     C.A.nbr = C.A.nbc = Nc;
     BD_TRY(spgemm<2>(Nc, Nc, L.R.rp.p, L.R.ci.p, L.R.v.p, AP.rp.p, AP.ci.p, AP.v.p, C.A.rp, C.A.ci,
-                     C.A.v, &cnb, s));
+                     C.A.v, &cnb, s, (double)apnb / std::max(N, 1)));
     C.A.nb = cnb;
     BD_CUDA(cudaStreamSynchronize(s));
     return BD_OK;
