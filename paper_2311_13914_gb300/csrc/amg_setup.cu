@@ -217,6 +217,114 @@ __global__ void k_spgemm_fill(int nrows, const int *__restrict__ arp, const int 
     (void)P2;
 }
 
+// Dense path with the row's accumulators and column marks in shared memory
+// (coarse levels: few columns), otherwise identical to k_spgemm_count /
+// k_spgemm_fill: a block per output row, every entry accumulated in ascending
+// middle index.  Shared memory: marks (ncols ints) for the count; marks,
+// accumulators (ncols x BB doubles) and the row's column list (P2 ints) for
+// the fill.
+__global__ void k_spgemm_count_smem(int nrows, const int *__restrict__ arp, const int *__restrict__ aci,
+                                    const int *__restrict__ brp, const int *__restrict__ bci, int ncols,
+                                    int *__restrict__ cnt)
+{
+    extern __shared__ int smark[];
+    __shared__ int count;
+    for (int j = threadIdx.x; j < ncols; j += blockDim.x) smark[j] = -1;
+    __syncthreads();
+    for (int i = blockIdx.x; i < nrows; i += gridDim.x) {
+        if (threadIdx.x == 0) count = 0;
+        __syncthreads();
+        for (int t = arp[i]; t < arp[i + 1]; t++) {
+            int k = aci[t];
+            for (int s2 = brp[k] + threadIdx.x; s2 < brp[k + 1]; s2 += blockDim.x) {
+                int j = bci[s2];
+                if (atomicExch(&smark[j], i) != i) atomicAdd(&count, 1);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) cnt[i] = count;
+        __syncthreads();
+    }
+}
+
+template <int BS>
+__global__ void k_spgemm_fill_smem(int nrows, const int *__restrict__ arp, const int *__restrict__ aci,
+                                   const double *__restrict__ av, const int *__restrict__ brp,
+                                   const int *__restrict__ bci, const double *__restrict__ bv, int ncols,
+                                   const int *__restrict__ crp, int *__restrict__ cci, double *__restrict__ cv)
+{
+    constexpr int BB = BS * BS;
+    extern __shared__ double sacc[];
+    int *mark = (int *)(sacc + (size_t)ncols * BB);
+    int *cols = mark + ncols;
+    __shared__ int count;
+    for (int j = threadIdx.x; j < ncols; j += blockDim.x) mark[j] = -1;
+    __syncthreads();
+    for (int i = blockIdx.x; i < nrows; i += gridDim.x) {
+        if (threadIdx.x == 0) count = 0;
+        __syncthreads();
+        for (int t = arp[i]; t < arp[i + 1]; t++) {
+            int k = aci[t];
+            double a[BB];
+#pragma unroll
+            for (int e = 0; e < BB; e++) a[e] = av[(size_t)t * BB + e];
+            for (int s2 = brp[k] + threadIdx.x; s2 < brp[k + 1]; s2 += blockDim.x) {
+                int j = bci[s2];
+                double *c = sacc + (size_t)j * BB;
+                if (mark[j] != i) {
+                    mark[j] = i;
+#pragma unroll
+                    for (int e = 0; e < BB; e++) c[e] = 0.0;
+                    cols[atomicAdd(&count, 1)] = j;
+                }
+                const double *b = bv + (size_t)s2 * BB;
+                if (BS == 1) {
+                    c[0] = c[0] + a[0] * b[0];
+                } else {
+                    // scalar middle index 2k then 2k+1
+                    c[0] = c[0] + a[0] * b[0];
+                    c[0] = c[0] + a[1] * b[2];
+                    c[1] = c[1] + a[0] * b[1];
+                    c[1] = c[1] + a[1] * b[3];
+                    c[2] = c[2] + a[2] * b[0];
+                    c[2] = c[2] + a[3] * b[2];
+                    c[3] = c[3] + a[2] * b[1];
+                    c[3] = c[3] + a[3] * b[3];
+                }
+            }
+            __syncthreads();
+        }
+        int n = count;
+        int p2 = 1;
+        while (p2 < n) p2 <<= 1;
+        for (int x = n + threadIdx.x; x < p2; x += blockDim.x) cols[x] = INT_MAX;
+        __syncthreads();
+        for (int kk = 2; kk <= p2; kk <<= 1)
+            for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                for (int x = threadIdx.x; x < p2; x += blockDim.x) {
+                    int y = x ^ jj;
+                    if (y > x) {
+                        bool up = (x & kk) == 0;
+                        int cx = cols[x], cy = cols[y];
+                        if ((cx > cy) == up) {
+                            cols[x] = cy;
+                            cols[y] = cx;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        int base = crp[i];
+        for (int x = threadIdx.x; x < n; x += blockDim.x) {
+            int j = cols[x];
+            cci[base + x] = j;
+#pragma unroll
+            for (int e = 0; e < BB; e++) cv[(size_t)(base + x) * BB + e] = sacc[(size_t)j * BB + e];
+        }
+        __syncthreads();
+    }
+}
+
 // Hash path for products with very many columns and short rows (the squared
 // strength graph of a large fine level): one warp per output row, open
 // addressing in shared memory, the same accumulation order.
@@ -493,7 +601,21 @@ static int spgemm(int nrows, int ncols, const int *arp, const int *aci, const do
     int HCn = 0;
     const int lanes = hash_lanes(b_per_row);
     ::bd::note_spgemm_path(dense);
-    if (dense) {
+    // the dense path keeps a row's accumulators in shared memory when they
+    // fit (with the largest column list a row can have)
+    const size_t dense_smem = (size_t)ncols * (BB * sizeof(double) + sizeof(int)) +
+                              (size_t)pow2_at_least(std::max(ncols, 1)) * sizeof(int);
+    const bool dense_in_smem = dense && dense_smem <= (200u << 10);
+    if (dense_in_smem) {
+        const size_t cs = (size_t)ncols * sizeof(int);
+        BD_CUDA(cudaFuncSetAttribute(k_spgemm_count_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)std::max<size_t>(cs, 4)));
+        const int gc = (int)std::min<long long>(nrows, (long long)kSM * 8);
+        k_spgemm_count_smem<<<std::max(gc, 1), 128, std::max<size_t>(cs, 4), s>>>(nrows, arp, aci, brp, bci, ncols,
+                                                                                   cnt.p);
+        ::bd::note_launch();
+        BD_LAUNCH_CHECK();
+    } else if (dense) {
         BD_TRY(mark.alloc((size_t)grid * ncols));
         BD_TRY(acc.alloc((size_t)grid * ncols * BB));
         BD_CUDA(cudaMemsetAsync(mark.p, 0xff, mark.bytes(), s));
@@ -527,7 +649,16 @@ static int spgemm(int nrows, int ncols, const int *arp, const int *aci, const do
     if (maxrow > kMaxSortSeg) return BD_ERANGE;
     BD_TRY(cci.alloc((size_t)total));
     BD_TRY(cv.alloc((size_t)total * BB));
-    if (dense) {
+    if (dense_in_smem) {
+        BD_CUDA(cudaFuncSetAttribute(k_spgemm_fill_smem<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)dense_smem));
+        const int per_sm = std::max(1, (int)((227u << 10) / (dense_smem + 1024)));
+        const int gf = (int)std::min<long long>(nrows, (long long)kSM * per_sm);
+        k_spgemm_fill_smem<BS><<<std::max(gf, 1), 256, dense_smem, s>>>(nrows, arp, aci, av, brp, bci, bv, ncols,
+                                                                         crp.p, cci.p, cv.p);
+        ::bd::note_launch();
+        BD_LAUNCH_CHECK();
+    } else if (dense) {
         int P2 = pow2_at_least(maxrow);
         BD_CUDA(cudaMemsetAsync(mark.p, 0xff, mark.bytes(), s));
         size_t smem = (size_t)P2 * sizeof(int);
