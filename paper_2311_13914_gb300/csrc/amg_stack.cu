@@ -137,6 +137,33 @@ struct StStore {  // q = A p (FP64, PCG)
     __device__ __forceinline__ void operator()(int p, double y0, double y1) const { q[p] = make_double2(y0, y1); }
 };
 
+// Finest level of the stack in sliced ELL with the shared Ki/Ke pattern of
+// the Bidomain operator (every member's own slices, its rows padded to whole
+// 32-row slices; padded rows, member -1, are skipped): one thread per row,
+// slot j of a slice holds entry j of its 32 rows; per node pair
+// a += Ki (v_q + u_q), b += Ke u_q, then y_v = c M_p v_p + a, y_u = a + b.
+template <class S, class E>
+__global__ void __launch_bounds__(256) k_st_sell(int rows, const int *__restrict__ mem, const int *__restrict__ sptr,
+                                                 const int *__restrict__ col, const v2<S> *__restrict__ kk,
+                                                 const S *__restrict__ cm, StGather<S> g, E epi)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < rows; p += gridDim.x * blockDim.x) {
+        if (mem[p] < 0) continue;
+        const int sl = p >> 5, lane = p & 31, j1 = sptr[sl + 1];
+        S a = 0, b = 0;
+#pragma unroll 4
+        for (int j = sptr[sl]; j < j1; j++) {
+            const size_t idx = (size_t)j * 32 + lane;
+            const v2<S> k = kk[idx];
+            const v2<S> x = g(col[idx]);
+            a = fma(k.x, x.x + x.y, a);
+            b = fma(k.y, x.y, b);
+        }
+        const v2<S> xp = g(p);
+        epi(p, fma(cm[p], xp.x, a), a + b);
+    }
+}
+
 // ------------------------------------------------------------------ assembly of the stack
 __global__ void k_st_shift(long long n, const int *__restrict__ src, int *__restrict__ dst, int add)
 {
@@ -432,7 +459,9 @@ template <class S>
 __global__ void k_st_p(int N, StPcg<S> v, const double *__restrict__ scal)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        const double *sc = scal + (size_t)v.mem[i] * T_NSLOTS;
+        const int m = v.mem[i];
+        if (m < 0) continue;  // padding of a member's last 32-row slice
+        const double *sc = scal + (size_t)m * T_NSLOTS;
         if (sc[T_ACTIVE] == 0.0) continue;
         double2 zi = v.z[i];
         zi.y -= sc[T_MEANZ];
@@ -453,6 +482,7 @@ __global__ void k_st_project_x(int N, double2 *__restrict__ x, const int *__rest
                                const double *__restrict__ scal)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        if (mem[i] < 0) continue;  // padding
         const double *sc = scal + (size_t)mem[i] * T_NSLOTS;
         double2 xi = x[i];
         if (!(sc[T_NF2] > 0.0)) xi = make_double2(0.0, 0.0);
@@ -475,6 +505,12 @@ struct StLevel {
     DBuf<double> coef;         // 3 per member
     DBuf<double> f, u, r, d, w, invd;          // FP64 V-cycle (f unused on the finest level)
     DBuf<float> f32, u32, r32, d32, w32, invd32;
+    // finest level only, when every member has its sliced-ELL finest level:
+    // the members' slices end to end (columns shifted to the stack's nodes)
+    bool sell = false;
+    DBuf<int> ssptr, scol;
+    DBuf<double> skk, scm;     // FP64 (the PCG's A p always; the FP64 V-cycle)
+    DBuf<float> skk32, scm32;  // FP32 V-cycle
 };
 
 }  // namespace bd
@@ -561,14 +597,13 @@ struct StPart {
     long long row0;
     long long col0;
 };
-int st_build(const std::vector<StPart> &parts, int ncols, bool fp64, bool fp32, BSR &O, DBuf<float> &O32,
-             cudaStream_t s)
+// rows: the stacked operator's rows, the parts' rows at their row0 (ascending)
+// and empty rows in between (the finest level's padding to 32-row slices)
+int st_build(const std::vector<StPart> &parts, long long rows, int ncols, bool fp64, bool fp32, BSR &O,
+             DBuf<float> &O32, cudaStream_t s)
 {
-    long long rows = 0, blocks = 0;
-    for (const StPart &pt : parts) {
-        rows += pt.nbr;
-        blocks += pt.nbr > 0 ? pt.M->nb : 0;  // full operators: nbr == M->nbr
-    }
+    long long blocks = 0;
+    for (const StPart &pt : parts) blocks += pt.nbr > 0 ? pt.M->nb : 0;  // full operators: nbr == M->nbr
     if (rows > 2147483647LL || blocks > 2147483647LL) return BD_ERANGE;
     O.nbr = (int)rows;
     O.nbc = ncols;
@@ -577,13 +612,65 @@ int st_build(const std::vector<StPart> &parts, int ncols, bool fp64, bool fp32, 
     BD_TRY(O.ci.alloc((size_t)std::max<long long>(blocks, 1)));
     if (fp64) BD_TRY(O.v.alloc(4 * (size_t)std::max<long long>(blocks, 1)));
     if (fp32) BD_TRY(O32.alloc(4 * (size_t)std::max<long long>(blocks, 1)));
-    long long blk = 0;
+    long long blk = 0, next = 0;
     for (const StPart &pt : parts) {
         if (pt.nbr <= 0) continue;
+        if (pt.row0 > next) {  // empty rows before this part
+            k_st_fill<<<grid_for(pt.row0 - next, 256), 256, 0, s>>>(pt.row0 - next, O.rp.p + next, (int)blk);
+            ::bd::note_launch();
+        }
         BD_TRY(st_append(*pt.M, pt.nbr, pt.v32, O, fp32 ? &O32 : nullptr, (int)pt.row0, blk, (int)pt.col0, fp64, s));
         blk += pt.M->nb;
+        next = pt.row0 + pt.nbr;
     }
-    k_st_set<<<1, 1, 0, s>>>(O.rp.p + rows, (int)blocks); ::bd::note_launch();
+    k_st_fill<<<grid_for(rows + 1 - next, 256), 256, 0, s>>>(rows + 1 - next, O.rp.p + next, (int)blocks);
+    ::bd::note_launch();
+    BD_LAUNCH_CHECK();
+    return BD_OK;
+}
+
+int st_sell_build(amg_stack *b, const std::vector<int> &order, const std::vector<long long> &off, cudaStream_t s)
+{
+    StLevel &S = b->lev[0];
+    long long slots = 0;
+    int nsl = 0;
+    for (int k : order) {
+        slots += b->h[k]->sell.slots;
+        nsl += b->h[k]->sell.nslices;
+    }
+    if (slots * 32 > 2147483647LL) return BD_ERANGE;
+    BD_TRY(S.ssptr.alloc((size_t)nsl + 1));
+    BD_TRY(S.scol.alloc((size_t)slots * 32));
+    BD_TRY(S.skk.alloc((size_t)slots * 64));
+    BD_TRY(S.scm.alloc((size_t)std::max(S.N, 1)));
+    BD_CUDA(cudaMemsetAsync(S.scm.p, 0, S.scm.bytes(), s));
+    if (b->p32) {
+        BD_TRY(S.skk32.alloc((size_t)slots * 64));
+        BD_TRY(S.scm32.alloc((size_t)std::max(S.N, 1)));
+        BD_CUDA(cudaMemsetAsync(S.scm32.p, 0, S.scm32.bytes(), s));
+    }
+    long long so = 0;
+    for (int k : order) {
+        const FineSell &F = b->h[k]->sell;
+        const int N = b->h[k]->lev[0].N;
+        const long long sl0 = off[k] / 32;  // the member's first slice (offsets are 32-aligned)
+        k_st_shift<<<grid_for(F.nslices, 256), 256, 0, s>>>(F.nslices, F.sptr.p, S.ssptr.p + sl0, (int)so);
+        ::bd::note_launch();
+        k_st_shift<<<grid_for(F.slots * 32, 256), 256, 0, s>>>(F.slots * 32, F.col.p, S.scol.p + so * 32, (int)off[k]);
+        ::bd::note_launch();
+        BD_CUDA(cudaMemcpyAsync(S.skk.p + so * 64, F.kk.p, sizeof(double) * 64 * (size_t)F.slots,
+                                cudaMemcpyDeviceToDevice, s));
+        BD_CUDA(cudaMemcpyAsync(S.scm.p + off[k], F.cm.p, sizeof(double) * (size_t)N, cudaMemcpyDeviceToDevice, s));
+        if (b->p32) {
+            BD_CUDA(cudaMemcpyAsync(S.skk32.p + so * 64, F.kk32.p, sizeof(float) * 64 * (size_t)F.slots,
+                                    cudaMemcpyDeviceToDevice, s));
+            BD_CUDA(cudaMemcpyAsync(S.scm32.p + off[k], F.cm32.p, sizeof(float) * (size_t)N,
+                                    cudaMemcpyDeviceToDevice, s));
+        }
+        so += F.slots;
+    }
+    k_st_set<<<1, 1, 0, s>>>(S.ssptr.p + nsl, (int)slots);
+    ::bd::note_launch();
     BD_LAUNCH_CHECK();
     return BD_OK;
 }
@@ -605,8 +692,12 @@ int st_create(amg_stack *b, cudaStream_t s)
         L = std::max(L, b->nlev[k]);
     }
     b->L = L;
+    bool sell0 = true;
+    for (int k = 0; k < count; k++) sell0 = sell0 && b->h[k]->sell.valid;
+    b->lev[0].sell = sell0;
     // member order and node offsets per level: smoothing members, then the
-    // members whose coarsest level it is
+    // members whose coarsest level it is; on a sliced-ELL finest level every
+    // member starts on a 32-row slice
     std::vector<std::vector<int>> order(L);
     std::vector<std::vector<long long>> off(L, std::vector<long long>(count, -1));
     for (int l = 0; l < L; l++) {
@@ -618,7 +709,8 @@ int st_create(amg_stack *b, cudaStream_t s)
                 if ((pass == 0 && last > l) || (pass == 1 && last == l)) {
                     order[l].push_back(k);
                     off[l][k] = o;
-                    o += b->h[k]->lev[l].N;
+                    const long long nk = b->h[k]->lev[l].N;
+                    o += (l == 0 && sell0) ? (nk + 31) / 32 * 32 : nk;
                     if (pass == 0) ns = (int)o;
                 }
             }
@@ -634,7 +726,7 @@ int st_create(amg_stack *b, cudaStream_t s)
         for (int k : order[l]) {
             const Level &Lk = b->h[k]->lev[l];
             const bool smooth = b->nlev[k] - 1 > l;
-            if (l == 0 || smooth)
+            if ((l == 0 && !sell0) || (l > 0 && smooth))
                 pa.push_back({&Lk.A, p32 ? Lk.A32.p : nullptr, Lk.A.nbr, off[l][k], off[l][k]});
             if (smooth) pp.push_back({&Lk.P, p32 ? Lk.P32.p : nullptr, Lk.P.nbr, off[l][k], off[l + 1][k]});
         }
@@ -643,14 +735,16 @@ int st_create(amg_stack *b, cudaStream_t s)
                 const Level &Lk = b->h[k]->lev[l];
                 pr.push_back({&Lk.R, p32 ? Lk.R32.p : nullptr, Lk.R.nbr, off[l + 1][k], off[l][k]});
             }
-        BD_TRY(st_build(pa, S.N, l == 0 || !p32, p32, S.A, S.A32, s));
+        BD_TRY(st_build(pa, l == 0 ? S.N : S.Ns, S.N, l == 0 || !p32, p32, S.A, S.A32, s));
         S.rowsA = S.A.nbr;
         if (!pp.empty()) {
-            BD_TRY(st_build(pp, b->lev[l + 1].N, !p32, p32, S.P, S.P32, s));
-            BD_TRY(st_build(pr, S.N, !p32, p32, S.R, S.R32, s));
+            BD_TRY(st_build(pp, S.Ns, b->lev[l + 1].N, !p32, p32, S.P, S.P32, s));
+            BD_TRY(st_build(pr, b->lev[l + 1].N, S.N, !p32, p32, S.R, S.R32, s));
         }
-        // node -> member, Chebyshev coefficients, inverse diagonals
+        if (l == 0 && sell0) BD_TRY(st_sell_build(b, order[0], off[0], s));
+        // node -> member (-1 on padding), Chebyshev coefficients, inverse diagonals
         BD_TRY(S.mem.alloc((size_t)std::max(S.N, 1)));
+        BD_CUDA(cudaMemsetAsync(S.mem.p, 0xff, S.mem.bytes(), s));
         std::vector<double> coef(3 * (size_t)count, 0.0);
         for (int k : order[l]) {
             const Level &Lk = b->h[k]->lev[l];
@@ -774,6 +868,30 @@ template <> StView<float> st_view<float>(amg_stack *b, int l)
             (float2 *)S.d32.p, (float2 *)S.w32.p, (const float2 *)S.invd32.p};
 }
 
+template <class S> const v2<S> *st_kk(const StLevel &Lv);
+template <> const double2 *st_kk<double>(const StLevel &Lv) { return (const double2 *)Lv.skk.p; }
+template <> const float2 *st_kk<float>(const StLevel &Lv) { return (const float2 *)Lv.skk32.p; }
+template <class S> const S *st_cm(const StLevel &Lv);
+template <> const double *st_cm<double>(const StLevel &Lv) { return Lv.scm.p; }
+template <> const float *st_cm<float>(const StLevel &Lv) { return Lv.scm32.p; }
+
+// Operator of stack level l on rows [0, rows): the finest level's sliced ELL
+// when built, block CSR otherwise.
+template <class S, class E>
+int st_apply(const StLevel &Lv, int l, int rows, const S *vals, const v2<S> *x, E e, cudaStream_t s)
+{
+    if (l == 0 && Lv.sell) {
+        if (rows <= 0) return BD_OK;
+        const int grid = (int)std::min<long long>(((long long)rows + 255) / 256, (long long)kSM * 8);
+        k_st_sell<S, E><<<grid, 256, 0, s>>>(rows, Lv.mem.p, Lv.ssptr.p, Lv.scol.p, st_kk<S>(Lv), st_cm<S>(Lv),
+                                             StGather<S>{x}, e);
+        ::bd::note_launch();
+        BD_LAUNCH_CHECK();
+        return BD_OK;
+    }
+    return launch_bsr_rows<S>(rows, Lv.A.rp.p, Lv.A.ci.p, vals, Lv.lanes[0], StGather<S>{x}, e, s);
+}
+
 template <class S>
 int st_vcycle(amg_stack *b, cudaStream_t s)
 {
@@ -783,10 +901,8 @@ int st_vcycle(amg_stack *b, cudaStream_t s)
         if (Lv.Ns <= 0) continue;
         const StView<S> v = st_view<S>(b, l), cv = st_view<S>(b, l + 1);
         const StCoef c{Lv.mem.p, Lv.coef.p}, cc{b->lev[l + 1].mem.p, b->lev[l + 1].coef.p};
-        BD_TRY(launch_bsr_rows<S>(Lv.Ns, Lv.A.rp.p, Lv.A.ci.p, v.Av, Lv.lanes[0], StGather<S>{v.d},
-                                  StPre<S>{v.f, v.invd, v.d, v.u, c}, s));
-        BD_TRY(launch_bsr_rows<S>(Lv.Ns, Lv.A.rp.p, Lv.A.ci.p, v.Av, Lv.lanes[0], StGather<S>{v.u},
-                                  StResid<S>{v.f, v.r}, s));
+        BD_TRY(st_apply<S>(Lv, l, Lv.Ns, v.Av, v.d, StPre<S>{v.f, v.invd, v.d, v.u, c}, s));
+        BD_TRY(st_apply<S>(Lv, l, Lv.Ns, v.Av, v.u, StResid<S>{v.f, v.r}, s));
         BD_TRY(launch_bsr<S>(Lv.R, v.Rv, Lv.lanes[1], StGather<S>{v.r}, StStoreD0<S>{cv.f, cv.d, cv.invd, cc}, s));
     }
     StLevelPtrs<S> lp{};
@@ -806,10 +922,8 @@ int st_vcycle(amg_stack *b, cudaStream_t s)
         const StView<S> v = st_view<S>(b, l), cv = st_view<S>(b, l + 1);
         const StCoef c{Lv.mem.p, Lv.coef.p};
         BD_TRY(launch_bsr<S>(Lv.P, v.Pv, Lv.lanes[2], StGather<S>{cv.u}, StAdd<S>{v.u}, s));
-        BD_TRY(launch_bsr_rows<S>(Lv.Ns, Lv.A.rp.p, Lv.A.ci.p, v.Av, Lv.lanes[0], StGather<S>{v.u},
-                                  StPost1<S>{v.f, v.invd, v.u, v.r, v.d, v.w, c}, s));
-        BD_TRY(launch_bsr_rows<S>(Lv.Ns, Lv.A.rp.p, Lv.A.ci.p, v.Av, Lv.lanes[0], StGather<S>{v.d},
-                                  StPost2<S>{v.r, v.d, v.invd, v.w, v.u, c}, s));
+        BD_TRY(st_apply<S>(Lv, l, Lv.Ns, v.Av, v.u, StPost1<S>{v.f, v.invd, v.u, v.r, v.d, v.w, c}, s));
+        BD_TRY(st_apply<S>(Lv, l, Lv.Ns, v.Av, v.d, StPost2<S>{v.r, v.d, v.invd, v.w, v.u, c}, s));
     }
     return BD_OK;
 }
@@ -846,6 +960,7 @@ StRed st_red(amg_stack *b, cudaGraphConditionalHandle cond)
 int st_apply_a(amg_stack *b, const double2 *x, double2 *q, cudaStream_t s)
 {
     StLevel &S = b->lev[0];
+    if (S.sell) return st_apply<double>(S, 0, S.N, nullptr, x, StStore{q}, s);
     return launch_bsr_rows<double>(S.N, S.A.rp.p, S.A.ci.p, S.A.v.p, lanes_for(S.A, false), StGather<double>{x},
                                    StStore{q}, s);
 }
