@@ -837,6 +837,8 @@ static int zo_streams(const ZOut *zo);
 template <class S, bool SU>
 static int launch_sell_z(amg_hierarchy *h, const LV<S> &lv, const EpiPost2<S, SU> &epi, const ZOut &zo,
                          cudaStream_t s);
+// FP32 V-cycle output to the PCG's z (FP64) with the z statistics in one pass
+static int launch_z_from32(amg_hierarchy *h, const float2 *u, const ZOut &zo, cudaStream_t s);
 
 // One V-cycle in precision S; f0/u0 are the finest level's right-hand side and
 // output (d0 of the finest level must already be in lev[0]'s d vector).  SU0:
@@ -899,7 +901,12 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
             int s2 = prof_begin(h, s, 16 * l + R_POST2, l == 0);
             const EpiPost2<S, SU> epi{lv.r, lv.d, lv.invd, lv.w, u, (S)L.ch_c1, (S)L.ch_c2};
             double bytes = l == 0 ? fine_bytes<S>(h, L, 5) : 0.0;
-            if (l == 0 && zo && h->sell.valid) {
+            // FP64: the post-smoother's last kernel carries the PCG's z statistics;
+            // FP32: the plain kernel, then one pass that converts u to z and sums
+            // the statistics (faster than carrying the FP64 work in the
+            // HBM-bound FP32 kernel, measured)
+            const bool fuse_z = l == 0 && zo && h->sell.valid && sizeof(S) == 8;
+            if (fuse_z) {
                 BD_TRY((launch_sell_z<S, SU>(h, lv, epi, *zo, s)));
                 if (zdone) *zdone = true;
                 // u is not stored; z written and the PCG's r (and z_old) read in FP64
@@ -907,8 +914,13 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
             } else {
                 BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{lv.d}, epi, s));
             }
-            prof_end(h, s2, bytes, fine_flops(h, L, SU), s,
-                     fine_ops<S>(h, L, (l == 0 && zo && h->sell.valid) ? FR_POST2Z : FR_POST2));
+            prof_end(h, s2, bytes, fine_flops(h, L, SU), s, fine_ops<S>(h, L, fuse_z ? FR_POST2Z : FR_POST2));
+            if (l == 0 && zo && sizeof(S) == 4) {
+                int sz = prof_begin(h, s, R_ZSTATS, false);
+                BD_TRY(launch_z_from32(h, (const float2 *)u, *zo, s));
+                prof_end(h, sz, 0.0, 0.0, s);
+                if (zdone) *zdone = true;
+            }
         } else {
             int s2 = prof_begin(h, s, 16 * l + R_POST2, false);
             k_copy2<S><<<grid_for(L.N, 256), 256, 0, s>>>(L.N, lv.w, u); ::bd::note_launch();
@@ -1405,6 +1417,34 @@ __global__ void __launch_bounds__(256, MINB) k_sell_z(int N, const int *__restri
 }
 
 static int zo_streams(const ZOut *zo) { return zo->zold ? 3 : 2; }
+
+// z = (double) u of the FP32 V-cycle, and its statistics (z_u, r_u, r.z,
+// r.z_old) in FP64 (stage 3), in one pass
+__global__ void k_z_from32(int N, const float2 *__restrict__ u, ZOut zo)
+{
+    double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+    for (int i = share_lo(N) + threadIdx.x, e = share_hi(N); i < e; i += blockDim.x) {
+        const float2 v = u[i];
+        const double2 z = make_double2((double)v.x, (double)v.y), r = zo.r[i];
+        zo.z[i] = z;
+        a += z.y;
+        b += r.y;
+        c += r.x * z.x + r.y * z.y;
+        if (zo.zold) {
+            const double2 o = zo.zold[i];
+            d += r.x * o.x + r.y * o.y;
+        }
+    }
+    block_finish<4>(a, b, c, d, zo.fin);
+}
+
+static int launch_z_from32(amg_hierarchy *h, const float2 *u, const ZOut &zo, cudaStream_t s)
+{
+    k_z_from32<<<kVecBlocks, kVecThreads, 0, s>>>(h->lev[0].N, u, zo);
+    ::bd::note_launch();
+    BD_LAUNCH_CHECK();
+    return BD_OK;
+}
 
 template <class S, bool SU>
 static int launch_sell_z(amg_hierarchy *h, const LV<S> &lv, const EpiPost2<S, SU> &epi, const ZOut &zo,
