@@ -36,6 +36,7 @@ struct Level {
     int N = 0;                 // nodes (unknowns 2N)
     BSR A;                     // operator
     DBuf<double> invdiag;      // 1 / A(i,i), 2N
+    DBuf<double> idc2, idt;    // FP64 sliced-ELL finest level: c2 / A(i,i) and 1 / (theta A(i,i))
     DBuf<double> B;            // near-null coefficients per field, 2N
     DBuf<unsigned char> mis;   // root flags (not on the coarsest)
     DBuf<int> agg;             // aggregate id per node

@@ -336,6 +336,62 @@ template <class S, bool SU = false> struct EpiPost2 {
     __device__ __forceinline__ void operator()(int p, S y0, S y1) const { u[p] = value(p, y0, y1); }
 };
 
+// The Chebyshev steps of the FP64 finest level written in the (v + u, u) form
+// of the vectors they gather, with the inverse diagonal scaled per level
+// (idc2 = c2 D^{-1}, idt = D^{-1}/theta): fewer FP64 operations per node on a
+// level bound by the FP64 pipe.  For u = d0 + (c1 d0 + c2 D^{-1} r) with
+// m = idc2 r: u_s = (1 + c1) d0_s + (m_v + m_u), u_u = (1 + c1) d0_u + m_u.
+struct EpiPreX {
+    const double2 *__restrict__ f;
+    const double2 *__restrict__ idc2;
+    const double2 *__restrict__ d0;  // (v + u, u)
+    double2 *__restrict__ u;         // (v + u, u)
+    double c1p;                      // 1 + c1
+    __device__ __forceinline__ void operator()(int p, double y0, double y1) const
+    {
+        const double2 fp = f[p], k = idc2[p], dp = d0[p];
+        const double m0 = k.x * (fp.x - y0), m1 = k.y * (fp.y - y1);
+        u[p] = make_double2(fma(c1p, dp.x, m0 + m1), fma(c1p, dp.y, m1));
+    }
+};
+// r = f - A u, d = D^{-1} r / theta, w = u + d: r plain, d and w in (v + u, u)
+struct EpiPost1X {
+    const double2 *__restrict__ f;
+    const double2 *__restrict__ idt;
+    const double2 *__restrict__ u;  // (v + u, u)
+    double2 *__restrict__ r;
+    double2 *__restrict__ d;
+    double2 *__restrict__ w;
+    __device__ __forceinline__ void operator()(int p, double y0, double y1) const
+    {
+        const double2 fp = f[p], k = idt[p], up = u[p];
+        const double r0 = fp.x - y0, r1 = fp.y - y1;
+        const double d1 = r1 * k.y, ds = r0 * k.x + d1;
+        r[p] = make_double2(r0, r1);
+        d[p] = make_double2(ds, d1);
+        w[p] = make_double2(up.x + ds, up.y + d1);
+    }
+};
+// u = w + (c1 d + c2 D^{-1} (r - A d)) in plain (v, u) form from w and d in
+// (v + u, u) form
+struct EpiPost2X {
+    const double2 *__restrict__ r;
+    const double2 *__restrict__ d;     // (v + u, u)
+    const double2 *__restrict__ idc2;
+    const double2 *__restrict__ w;     // (v + u, u)
+    double2 *__restrict__ u;
+    double c1;
+    __device__ __forceinline__ double2 value(int p, double y0, double y1) const
+    {
+        const double2 rp_ = r[p], dp = d[p], k = idc2[p], wp = w[p];
+        const double m0 = k.x * (rp_.x - y0), m1 = k.y * (rp_.y - y1);
+        const double uu = wp.y + fma(c1, dp.y, m1);
+        const double us = wp.x + fma(c1, dp.x, m0 + m1);
+        return make_double2(us - uu, uu);
+    }
+    __device__ __forceinline__ void operator()(int p, double y0, double y1) const { u[p] = value(p, y0, y1); }
+};
+
 // ------------------------------------------------------------------ per-level views
 // Value and vector pointers of one level in precision S (index arrays are shared).
 template <class S> struct LV {
@@ -347,6 +403,34 @@ template <class S> struct LV {
 };
 
 template <class S> static LV<S> view(amg_hierarchy *h, int l);
+
+// The smoothing epilogues of a level: the (v + u, u)-form ones with scaled
+// inverse diagonals on the FP64 sliced-ELL finest level (SU), the plain ones
+// elsewhere.
+template <class S, bool SU>
+static auto epi_pre(const Level &L, const LV<S> &lv, const v2<S> *f, v2<S> *d0, v2<S> *u)
+{
+    if constexpr (SU && std::is_same<S, double>::value)
+        return EpiPreX{f, (const double2 *)L.idc2.p, d0, u, 1.0 + L.ch_c1};
+    else
+        return EpiPre<S, SU>{f, lv.invd, d0, u, (S)L.ch_c1, (S)L.ch_c2};
+}
+template <class S, bool SU>
+static auto epi_post1(const Level &L, const LV<S> &lv, const v2<S> *f, v2<S> *u)
+{
+    if constexpr (SU && std::is_same<S, double>::value)
+        return EpiPost1X{f, (const double2 *)L.idt.p, u, lv.r, lv.d, lv.w};
+    else
+        return EpiPost1<S, SU>{f, lv.invd, u, lv.r, lv.d, lv.w, (S)L.ch_inv_theta};
+}
+template <class S, bool SU>
+static auto epi_post2(const Level &L, const LV<S> &lv, v2<S> *u)
+{
+    if constexpr (SU && std::is_same<S, double>::value)
+        return EpiPost2X{lv.r, lv.d, (const double2 *)L.idc2.p, lv.w, u, L.ch_c1};
+    else
+        return EpiPost2<S, SU>{lv.r, lv.d, lv.invd, lv.w, u, (S)L.ch_c1, (S)L.ch_c2};
+}
 template <> LV<double> view<double>(amg_hierarchy *h, int l)
 {
     Level &L = h->lev[l];
@@ -700,9 +784,9 @@ static double fine_flops(const amg_hierarchy *h, const Level &L, bool su)
 // each: what the pipe issues) of one finest-level launch of the FP64 V-cycle
 // or of the PCG's A p: per stored slot the 2 FMA of the (v + u, u) form, per
 // node the row tail (c M v + a, a + b, and v = (v + u) - u) and the fused
-// step as written in its epilogue: pre-smoother 12, residual 2, first
-// post-smoothing half 9, second half 12 (17 with the PCG's z statistics),
-// A p with p.Ap 3.  The FP32 V-cycle's launches issue FP64 operations only
+// step as written in its epilogue: pre-smoother 7, residual 2, first
+// post-smoothing half 6, second half 10 (14 with the PCG's z statistics),
+// A p with p.Ap 2.  The FP32 V-cycle's launches issue FP64 operations only
 // for the z statistics (conversions and sums, 10 per node).  Block-CSR finest
 // levels: 4 FMA per 2x2 block, epilogues not counted.
 enum FineRole { FR_PRE, FR_RESID, FR_POST1, FR_POST2, FR_POST2Z, FR_AP };
@@ -711,7 +795,7 @@ static double fine_ops(const amg_hierarchy *h, const Level &L, int role)
 {
     if (!h->sell.valid) return sizeof(S) == 8 || role == FR_AP ? 4.0 * (double)L.A.nb : 0.0;
     if (sizeof(S) == 4 && role != FR_AP) return role == FR_POST2Z ? 10.0 * L.N : 0.0;
-    static const double epi[] = {12.0, 2.0, 9.0, 12.0, 17.0, 3.0};
+    static const double epi[] = {7.0, 2.0, 6.0, 10.0, 14.0, 2.0};
     return 2.0 * 32.0 * (double)h->sell.slots + (3.0 + epi[role]) * (double)L.N;
 }
 
@@ -823,6 +907,13 @@ __global__ void k_out64(int N, const float2 *__restrict__ u, double2 *__restrict
     }
 }
 
+__global__ void k_scale_vec(long long n, const double *__restrict__ a, double c, double *__restrict__ b)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        b[i] = c * a[i];
+}
+
 __global__ void k_to_f32(long long n, const double *__restrict__ a, float *__restrict__ b)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -834,9 +925,8 @@ __global__ void k_to_f32(long long n, const double *__restrict__ a, float *__res
 // (defined with the PCG reductions below).
 struct ZOut;
 static int zo_streams(const ZOut *zo);
-template <class S, bool SU>
-static int launch_sell_z(amg_hierarchy *h, const LV<S> &lv, const EpiPost2<S, SU> &epi, const ZOut &zo,
-                         cudaStream_t s);
+template <class S, bool SU, class E2>
+static int launch_sell_z(amg_hierarchy *h, const LV<S> &lv, const E2 &epi, const ZOut &zo, cudaStream_t s);
 // FP32 V-cycle output to the PCG's z (FP64) with the z statistics in one pass
 static int launch_z_from32(amg_hierarchy *h, const float2 *u, const ZOut &zo, cudaStream_t s);
 
@@ -862,8 +952,7 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
         v2<S> *d0 = lv.d;
         if (deg2) {
             int sl = prof_begin(h, s, 16 * l + R_PRE, l == 0);
-            BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{d0},
-                                   EpiPre<S, SU>{f, lv.invd, d0, u, (S)L.ch_c1, (S)L.ch_c2}, s));
+            BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{d0}, epi_pre<S, SU>(L, lv, f, d0, u), s));
             prof_end(h, sl, l == 0 ? fine_bytes<S>(h, L, 4) : 0.0, fine_flops(h, L, SU), s, fine_ops<S>(h, L, FR_PRE));
         } else {
             int sl = prof_begin(h, s, 16 * l + R_PRE, false);
@@ -894,12 +983,11 @@ static int vcycle_impl(amg_hierarchy *h, const v2<S> *f0, v2<S> *u0, cudaStream_
                              EpiAdd<S, SU>{u}, s));
         prof_end(h, sp, 0.0, 0.0, s);
         int s1 = prof_begin(h, s, 16 * l + R_POST1, l == 0);
-        BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{u},
-                               EpiPost1<S, SU>{f, lv.invd, u, lv.r, lv.d, lv.w, (S)L.ch_inv_theta}, s));
+        BD_TRY(apply_level<SU>(h, l, lv, GatherVec<S>{u}, epi_post1<S, SU>(L, lv, f, u), s));
         prof_end(h, s1, l == 0 ? fine_bytes<S>(h, L, 6) : 0.0, fine_flops(h, L, SU), s, fine_ops<S>(h, L, FR_POST1));
         if (deg2) {
             int s2 = prof_begin(h, s, 16 * l + R_POST2, l == 0);
-            const EpiPost2<S, SU> epi{lv.r, lv.d, lv.invd, lv.w, u, (S)L.ch_c1, (S)L.ch_c2};
+            const auto epi = epi_post2<S, SU>(L, lv, u);
             double bytes = l == 0 ? fine_bytes<S>(h, L, 5) : 0.0;
             // FP64: the post-smoother's last kernel carries the PCG's z statistics;
             // FP32: the plain kernel, then one pass that converts u to z and sums
@@ -1313,7 +1401,7 @@ __global__ void __launch_bounds__(256, 4) k_sell_reduce(int N, const int *__rest
         const double y0 = fma(cm[p], vp, a), y1 = a + b;
         if (MODE == 0) {
             out[p] = make_double2(y0, y1);
-            acc += vp * y0 + up * y1;
+            acc = fma(vp, y0, fma(up, y1, acc));
         } else {
             const double2 fp = f[p];
             const double r0 = fp.x - y0, r1 = fp.y - y1;
@@ -1386,12 +1474,12 @@ struct ZOut {
 // partials in FP64.  That keeps the kernel within 32 registers, so it runs 8
 // blocks per SM like the other FP32 finest-level kernels, which need every
 // resident warp to keep enough bytes in flight.
-template <class S, bool SU, int MINB>
+template <class S, bool SU, int MINB, class E2>
 __global__ void __launch_bounds__(256, MINB) k_sell_z(int N, const int *__restrict__ sptr,
                                                     const int *__restrict__ col,
                                                     const unsigned char *__restrict__ code, Stencil st,
                                                     const v2<S> *__restrict__ kk, const S *__restrict__ cm,
-                                                    GatherVec<S> gather, EpiPost2<S, SU> epi, ZOut zo)
+                                                    GatherVec<S> gather, E2 epi, ZOut zo)
 {
     __shared__ int off[27];
     if (sizeof(S) == 4) stage_stencil(st, off);
@@ -1407,10 +1495,10 @@ __global__ void __launch_bounds__(256, MINB) k_sell_z(int N, const int *__restri
         const S rx = (S)r.x, ry = (S)r.y;
         a += u.y;
         b += ry;
-        c += rx * u.x + ry * u.y;
+        c = fma(rx, u.x, fma(ry, u.y, c));
         if (zo.zold) {
             const double2 o = zo.zold[p];
-            d += rx * (S)o.x + ry * (S)o.y;
+            d = fma(rx, (S)o.x, fma(ry, (S)o.y, d));
         }
     }
     block_finish<4, 256>((double)a, (double)b, (double)c, (double)d, zo.fin);
@@ -1446,15 +1534,14 @@ static int launch_z_from32(amg_hierarchy *h, const float2 *u, const ZOut &zo, cu
     return BD_OK;
 }
 
-template <class S, bool SU>
-static int launch_sell_z(amg_hierarchy *h, const LV<S> &lv, const EpiPost2<S, SU> &epi, const ZOut &zo,
-                         cudaStream_t s)
+template <class S, bool SU, class E2>
+static int launch_sell_z(amg_hierarchy *h, const LV<S> &lv, const E2 &epi, const ZOut &zo, cudaStream_t s)
 {
     const FineSell &F = h->sell;
     const int N = h->lev[0].N;
     constexpr int MB = sizeof(S) == 8 ? 4 : 8;
     const int grid = (int)std::min<long long>(((long long)N + 31) / 32, (long long)kSM * MB);
-    k_sell_z<S, SU, MB><<<grid, 256, 0, s>>>(N, F.sptr.p, F.col.p, F.code.p, stencil_of(F), lv.kk, lv.cm,
+    k_sell_z<S, SU, MB, E2><<<grid, 256, 0, s>>>(N, F.sptr.p, F.col.p, F.code.p, stencil_of(F), lv.kk, lv.cm,
                                              GatherVec<S>{lv.d}, epi, zo);
     ::bd::note_launch();
     BD_LAUNCH_CHECK();
@@ -1695,6 +1782,16 @@ int prepare_solve(amg_hierarchy *h, cudaStream_t s)
             L.ch_inv_theta = 1.0 / theta;
             L.ch_c1 = rho1 * rho0;
             L.ch_c2 = 2.0 * rho1 / delta;
+            if (l == 0 && !p32 && h->sell.valid) {
+                // the FP64 finest level's scaled inverse diagonals (EpiPreX and kin)
+                BD_TRY(L.idc2.alloc(n));
+                BD_TRY(L.idt.alloc(n));
+                k_scale_vec<<<grid_for(n, 256), 256, 0, s>>>((long long)n, L.invdiag.p, L.ch_c2, L.idc2.p);
+                ::bd::note_launch();
+                k_scale_vec<<<grid_for(n, 256), 256, 0, s>>>((long long)n, L.invdiag.p, L.ch_inv_theta, L.idt.p);
+                ::bd::note_launch();
+                BD_LAUNCH_CHECK();
+            }
         }
     }
     if (p32 && h->sell.valid) {
