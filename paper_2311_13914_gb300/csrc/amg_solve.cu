@@ -784,7 +784,7 @@ static double fine_flops(const amg_hierarchy *h, const Level &L, bool su)
 // each: what the pipe issues) of one finest-level launch of the FP64 V-cycle
 // or of the PCG's A p: per stored slot the 2 FMA of the (v + u, u) form, per
 // node the row tail (c M v + a, a + b, and v = (v + u) - u) and the fused
-// step as written in its epilogue: pre-smoother 7, residual 2, first
+// step as its epilogue issues it: pre-smoother 6, residual 2, first
 // post-smoothing half 6, second half 10 (14 with the PCG's z statistics),
 // A p with p.Ap 2.  The FP32 V-cycle's launches issue FP64 operations only
 // for the z statistics (conversions and sums, 10 per node).  Block-CSR finest
@@ -795,7 +795,7 @@ static double fine_ops(const amg_hierarchy *h, const Level &L, int role)
 {
     if (!h->sell.valid) return sizeof(S) == 8 || role == FR_AP ? 4.0 * (double)L.A.nb : 0.0;
     if (sizeof(S) == 4 && role != FR_AP) return role == FR_POST2Z ? 10.0 * L.N : 0.0;
-    static const double epi[] = {7.0, 2.0, 6.0, 10.0, 14.0, 2.0};
+    static const double epi[] = {6.0, 2.0, 6.0, 10.0, 14.0, 2.0};
     return 2.0 * 32.0 * (double)h->sell.slots + (3.0 + epi[role]) * (double)L.N;
 }
 
