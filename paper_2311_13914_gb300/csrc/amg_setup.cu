@@ -580,22 +580,22 @@ static int spgemm(int nrows, int ncols, const int *arp, const int *aci, const do
     int grid = (int)g;
     DBuf<int> mark;
     DBuf<double> acc;
-    DBuf<int> flag;
-    BD_TRY(flag.alloc(1));
-    BD_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+    DBuf<int> flag;  // [0] hash-table overflow, [1] largest product bound, [2] longest output row
+    BD_TRY(flag.alloc(3));
+    BD_CUDA(cudaMemsetAsync(flag.p, 0, 3 * sizeof(int), s));
     // Rows with few products (the fine levels' many short rows) go to the
     // warp-per-row hash path: the dense path's thread block per row then idles
     // most of its threads and synchronises once per middle index.  Both paths
     // accumulate every entry in the same order, so the choice changes no bit.
-    std::vector<int> ub;
     long long mub = 1;
     if (nrows > 0) {
         k_spgemm_bound<<<(nrows + 255) / 256, 256, 0, s>>>(nrows, arp, aci, brp, cnt.p); ::bd::note_launch();
         BD_LAUNCH_CHECK();
-        ub.resize((size_t)nrows);
-        BD_CUDA(cudaMemcpyAsync(ub.data(), cnt.p, ub.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+        BD_TRY(device_max(cnt.p, nrows, flag.p + 1, s));
+        int hb = 0;
+        BD_CUDA(cudaMemcpyAsync(&hb, flag.p + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
         BD_CUDA(cudaStreamSynchronize(s));
-        for (int i = 0; i < nrows; i++) mub = std::max<long long>(mub, ub[i]);
+        mub = std::max<long long>(mub, hb);
         if (mub <= kHashProducts) dense = false;
     }
     int HCn = 0;
@@ -636,16 +636,14 @@ static int spgemm(int nrows, int ncols, const int *arp, const int *aci, const do
         default: BD_TRY(launch_count_hash<32>(nrows, HCs, arp, aci, brp, bci, cnt.p, flag.p, s)); break;
         }
     }
+    BD_TRY(device_max(cnt.p, nrows, flag.p + 2, s));  // cnt: the output row lengths
     long long total = 0;
     BD_TRY(exclusive_scan(cnt.p, crp.p, nrows, &total, s));
-    std::vector<int> hrp((size_t)nrows + 1);
-    BD_CUDA(cudaMemcpyAsync(hrp.data(), crp.p, hrp.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
-    int hflag = 0;
-    BD_CUDA(cudaMemcpyAsync(&hflag, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int hf[3] = {0, 0, 0};
+    BD_CUDA(cudaMemcpyAsync(hf, flag.p, sizeof(hf), cudaMemcpyDeviceToHost, s));
     BD_CUDA(cudaStreamSynchronize(s));
-    if (hflag) return BD_ERANGE;
-    int maxrow = 0;
-    for (int i = 0; i < nrows; i++) maxrow = std::max(maxrow, hrp[i + 1] - hrp[i]);
+    if (hf[0]) return BD_ERANGE;
+    const int maxrow = hf[2];
     if (maxrow > kMaxSortSeg) return BD_ERANGE;
     BD_TRY(cci.alloc((size_t)total));
     BD_TRY(cv.alloc((size_t)total * BB));
@@ -1053,7 +1051,7 @@ static int bsr_transpose(const BSR &a, BSR &t, cudaStream_t s)
     t.nbc = a.nbr;
     t.nb = a.nb;
     DBuf<int> cnt, fill, perm;
-    BD_TRY(cnt.alloc((size_t)a.nbc + 1));
+    BD_TRY(cnt.alloc((size_t)a.nbc + 2));  // counts, then the largest at [a.nbc + 1]
     BD_TRY(fill.alloc((size_t)a.nbc + 1));
     BD_TRY(perm.alloc((size_t)a.nb));
     BD_TRY(t.rp.alloc((size_t)a.nbc + 1));
@@ -1063,16 +1061,15 @@ static int bsr_transpose(const BSR &a, BSR &t, cudaStream_t s)
     BD_CUDA(cudaMemsetAsync(fill.p, 0, fill.bytes(), s));
     k_count_cols<<<(int)((a.nb + 255) / 256), 256, 0, s>>>(a.nb, a.ci.p, cnt.p); ::bd::note_launch();
     BD_LAUNCH_CHECK();
+    BD_TRY(device_max(cnt.p, a.nbc, cnt.p + a.nbc + 1, s));
     long long tot = 0;
-    BD_TRY(exclusive_scan(cnt.p, t.rp.p, a.nbc, &tot, s));
+    BD_TRY(exclusive_scan(cnt.p, t.rp.p, a.nbc, &tot, s));  // stream synchronised
+    int mx = 0;
+    BD_CUDA(cudaMemcpyAsync(&mx, cnt.p + a.nbc + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BD_CUDA(cudaStreamSynchronize(s));
     k_scatter_t<<<(a.nbr + 255) / 256, 256, 0, s>>>(a.nbr, a.rp.p, a.ci.p, t.rp.p, fill.p, t.ci.p,
                                                     perm.p); ::bd::note_launch();
     BD_LAUNCH_CHECK();
-    std::vector<int> h((size_t)a.nbc + 1);
-    BD_CUDA(cudaMemcpyAsync(h.data(), t.rp.p, h.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
-    BD_CUDA(cudaStreamSynchronize(s));
-    int mx = 0;
-    for (int j = 0; j < a.nbc; j++) mx = std::max(mx, h[j + 1] - h[j]);
     BD_TRY(sort_segments(t.ci.p, perm.p, t.rp.p, a.nbc, mx, s));
     k_gather_t<<<(int)((a.nb + 255) / 256), 256, 0, s>>>(a.nb, perm.p, a.v.p, t.v.p); ::bd::note_launch();
     BD_LAUNCH_CHECK();
@@ -1410,24 +1407,21 @@ static int coarsen_level(amg_hierarchy *h, int l, bool &is_coarsest, cudaStream_
     // a4 tentative prolongator and coarse near-null coefficients
     DBuf<int> moff, mfill, members;
     BD_TRY(moff.alloc((size_t)Nc + 1));
-    BD_TRY(mfill.alloc((size_t)Nc + 1));
+    BD_TRY(mfill.alloc((size_t)Nc + 2));  // counts, then the largest at [Nc + 1]
     BD_TRY(members.alloc((size_t)N));
     BD_CUDA(cudaMemsetAsync(mfill.p, 0, mfill.bytes(), s));
     k_count_members<<<nblk(N), 256, 0, s>>>(N, L.agg.p, mfill.p); ::bd::note_launch();
     BD_LAUNCH_CHECK();
+    BD_TRY(device_max(mfill.p, Nc, mfill.p + Nc + 1, s));
     long long tot = 0;
-    BD_TRY(exclusive_scan(mfill.p, moff.p, Nc, &tot, s));
+    BD_TRY(exclusive_scan(mfill.p, moff.p, Nc, &tot, s));  // stream synchronised
+    int mx = 0;
+    BD_CUDA(cudaMemcpyAsync(&mx, mfill.p + Nc + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BD_CUDA(cudaStreamSynchronize(s));
     BD_CUDA(cudaMemsetAsync(mfill.p, 0, mfill.bytes(), s));
     k_scatter_members<<<nblk(N), 256, 0, s>>>(N, L.agg.p, moff.p, mfill.p, members.p); ::bd::note_launch();
     BD_LAUNCH_CHECK();
-    {
-        std::vector<int> ho((size_t)Nc + 1);
-        BD_CUDA(cudaMemcpyAsync(ho.data(), moff.p, ho.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
-        BD_CUDA(cudaStreamSynchronize(s));
-        int mx = 0;
-        for (int J = 0; J < Nc; J++) mx = std::max(mx, ho[J + 1] - ho[J]);
-        BD_TRY(sort_segments(members.p, nullptr, moff.p, Nc, mx, s));
-    }
+    BD_TRY(sort_segments(members.p, nullptr, moff.p, Nc, mx, s));
     Level &C = h->lev[l + 1];
     C.N = Nc;
     BD_TRY(C.B.alloc(2 * (size_t)Nc));

@@ -112,6 +112,10 @@ inline int grid_for(long long work, int block, int per_sm_cap = 8) {
 // total on the host (stream synchronised).  BD_ERANGE if the total exceeds 2^31-1.
 int exclusive_scan(const int *in, int *out, int n, long long *total, cudaStream_t s);
 
+// *slot = max(0, a[0..n)) on the device, stream-ordered (slot: one device int;
+// the caller reads it back after its next synchronisation).
+int device_max(const int *a, int n, int *slot, cudaStream_t s);
+
 // Sort the keys of every segment [seg[i], seg[i+1]) ascending (keys unique
 // within a segment), permuting `payload` alongside when it is not NULL.
 // BD_ERANGE if a segment is longer than kMaxSortSeg.

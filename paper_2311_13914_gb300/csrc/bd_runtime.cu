@@ -135,6 +135,27 @@ int exclusive_scan(const int *in, int *out, int n, long long *total, cudaStream_
     return BD_OK;
 }
 
+// ------------------------------------------------------------------ maximum
+// Warp maxima combined by atomicMax: the result does not depend on the order.
+__global__ void k_max_int(const int *__restrict__ a, int n, int *out)
+{
+    int m = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        m = max(m, a[i]);
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
+}
+
+int device_max(const int *a, int n, int *slot, cudaStream_t s)
+{
+    BD_CUDA(cudaMemsetAsync(slot, 0, sizeof(int), s));
+    if (n <= 0) return BD_OK;
+    k_max_int<<<grid_for(n, 256), 256, 0, s>>>(a, n, slot); ::bd::note_launch();
+    BD_LAUNCH_CHECK();
+    return BD_OK;
+}
+
 // ------------------------------------------------------------------ segmented sort
 // One block per segment, bitonic sort in shared memory (padded to a power of 2).
 __global__ void k_sort_segments(int *keys, int *payload, const int *seg, int nseg, int P)
