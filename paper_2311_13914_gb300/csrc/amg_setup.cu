@@ -1190,19 +1190,25 @@ __global__ void k_gj_pivot(int n, int K, int bb, const double *__restrict__ A, d
 {
     __shared__ double D[kGJ][kGJ + 1];
     __shared__ double prow[kGJ], pcol[kGJ];
+    __shared__ double srp;
     for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) D[e / bb][e % bb] = A[(size_t)(K + e / bb) * n + K + e % bb];
     __syncthreads();
     for (int k = 0; k < bb; k++) {
-        // one division per pivot: the pivot row is scaled by its reciprocal
-        // (FP64 division is a long sequence on the FP64 pipe, and one thread
-        // block does all of this)
-        const double piv = D[k][k], rpiv = 1.0 / piv;
+        // one division per pivot, by one thread: the pivot row is scaled by its
+        // reciprocal (FP64 division is a long sequence on the FP64 pipe, and one
+        // thread block does all of this)
+        if (threadIdx.x == 0) {
+            const double piv = D[k][k];
+            srp = 1.0 / piv;
+            if (!(piv > 0.0)) *bad = 1;
+        }
+        __syncthreads();
+        const double rpiv = srp;
         if (threadIdx.x < bb) {
             prow[threadIdx.x] = D[k][threadIdx.x] * rpiv;
             pcol[threadIdx.x] = D[threadIdx.x][k];
         }
         __syncthreads();
-        if (threadIdx.x == 0 && !(piv > 0.0)) *bad = 1;
         for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) {
             const int i = e / bb, j = e % bb;
             double a;
@@ -1218,58 +1224,76 @@ __global__ void k_gj_pivot(int n, int K, int bb, const double *__restrict__ A, d
 }
 
 // W[k][j] = sum_m Dinv[k][m] A[K+m][j] for every column j (bb x n), and a copy
-// Cb of the pivot columns A[:, P] (the update overwrites them)
+// Cb of the pivot columns A[:, P] (the update overwrites them).  blockIdx.y
+// takes kGJ / kGJPanelK rows k of W, so the panel spreads over the GPU.
+constexpr int kGJPanelK = 4;
 __global__ void k_gj_panel(int n, int K, int bb, const double *__restrict__ A, const double *__restrict__ Dinv,
                            double *__restrict__ W, double *__restrict__ Cb)
 {
-    __shared__ double Di[kGJ * kGJ];
-    for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) Di[e] = Dinv[e];
+    __shared__ double Di[kGJPanelK][kGJ];
+    const int k0 = blockIdx.y * kGJPanelK;
+    for (int e = threadIdx.x; e < kGJPanelK * kGJ; e += blockDim.x) {
+        const int k = k0 + e / kGJ, m = e % kGJ;
+        Di[e / kGJ][m] = k < bb && m < bb ? Dinv[k * bb + m] : 0.0;
+    }
     __syncthreads();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    for (int m = 0; m < kGJ; m++) Cb[(size_t)j * kGJ + m] = m < bb ? A[(size_t)j * n + K + m] : 0.0;
+    if (j >= n || k0 >= bb) return;
+    if (blockIdx.y == 0)
+        for (int m = 0; m < kGJ; m++) Cb[(size_t)j * kGJ + m] = m < bb ? A[(size_t)j * n + K + m] : 0.0;
     double col[kGJ];
 #pragma unroll
     for (int m = 0; m < kGJ; m++) col[m] = m < bb ? A[(size_t)(K + m) * n + j] : 0.0;
-    for (int k = 0; k < bb; k++) {
+#pragma unroll
+    for (int kk = 0; kk < kGJPanelK; kk++) {
+        const int k = k0 + kk;
+        if (k >= bb) break;
         double w = 0.0;
 #pragma unroll
-        for (int m = 0; m < kGJ; m++)
-            if (m < bb) w = fma(Di[k * bb + m], col[m], w);
+        for (int m = 0; m < kGJ; m++) w = fma(Di[kk][m], col[m], w);
         W[(size_t)k * n + j] = w;
     }
 }
 
-// rows [32 blockIdx.y, +32), columns blockIdx.x * blockDim.x + threadIdx.x
+// Column chunk blockIdx.x * blockDim.x + threadIdx.x, rows [r0, r1): an equal
+// share of the n rows for each of the gridDim.y blocks of a column chunk (the
+// grid is one resident wave), taken kGJ rows at a time through shared memory.
 __global__ void k_gj_update(int n, int K, int bb, double *__restrict__ A, const double *__restrict__ Dinv,
                             const double *__restrict__ W, const double *__restrict__ Cb)
 {
-    __shared__ double C[kGJ][kGJ];  // A[i, P] of the block's rows, from the copy
-    const int r0 = blockIdx.y * kGJ;
-    for (int e = threadIdx.x; e < kGJ * kGJ; e += blockDim.x) {
-        const int r = e / kGJ, m = e % kGJ;
-        C[r][m] = r0 + r < n ? Cb[(size_t)(r0 + r) * kGJ + m] : 0.0;
-    }
-    __syncthreads();
+    __shared__ double C[kGJ][kGJ];  // A[i, P] of kGJ rows, from the copy
+    const int r0 = (int)((long long)n * blockIdx.y / gridDim.y);
+    const int r1 = (int)((long long)n * (blockIdx.y + 1) / gridDim.y);
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
+    const bool act = j < n;
     const bool jp = j >= K && j < K + bb;
     double w[kGJ];
 #pragma unroll
     for (int m = 0; m < kGJ; m++)
-        w[m] = m < bb ? (jp ? Dinv[m * bb + (j - K)] : W[(size_t)m * n + j]) : 0.0;
-    for (int r = 0; r < kGJ; r++) {
-        const int i = r0 + r;
-        if (i >= n) break;
-        const size_t e = (size_t)i * n + j;
-        if (i >= K && i < K + bb) {       // pivot row: W, with D^-1 in the pivot columns
-            A[e] = w[i - K];
-            continue;
+        w[m] = act && m < bb ? (jp ? Dinv[m * bb + (j - K)] : W[(size_t)m * n + j]) : 0.0;
+    for (int rb = r0; rb < r1; rb += kGJ) {
+        const int nr = min(kGJ, r1 - rb);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kGJ * kGJ; e += blockDim.x) {
+            const int r = e / kGJ, m = e % kGJ;
+            C[r][m] = r < nr ? Cb[(size_t)(rb + r) * kGJ + m] : 0.0;
         }
-        double a = jp ? 0.0 : A[e];
+        __syncthreads();
+        if (!act) continue;
+        for (int r = 0; r < nr; r++) {
+            const int i = rb + r;
+            const size_t e = (size_t)i * n + j;
+            if (i >= K && i < K + bb) {  // pivot row: W, with D^-1 in the pivot columns
+                // (read from W and D^-1 again: a dynamic index into w would put w in
+                // local memory for every multiply-add of the update)
+                A[e] = jp ? Dinv[(i - K) * bb + (j - K)] : W[(size_t)(i - K) * n + j];
+                continue;
+            }
+            double a = jp ? 0.0 : A[e];
 #pragma unroll
-        for (int m = 0; m < kGJ; m++) a = fma(-C[r][m], w[m], a);
-        A[e] = a;
+            for (int m = 0; m < kGJ; m++) a = fma(-C[r][m], w[m], a);
+            A[e] = a;
+        }
     }
 }
 
@@ -1554,11 +1578,16 @@ static int build_coarsest(amg_hierarchy *h, int l, cudaStream_t s)
         BD_TRY(Dinv.alloc((size_t)kGJ * kGJ));
         BD_TRY(W.alloc((size_t)kGJ * n));
         BD_TRY(Cb.alloc((size_t)kGJ * n));
-        const dim3 gu((n + 127) / 128, (n + kGJ - 1) / kGJ);
+        // the update as one resident wave: column chunks x equal row shares
+        int occ = 0;
+        BD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gj_update, 128, 0));
+        const int gx = (n + 127) / 128;
+        const int gy = std::max(1, std::min((kSM * std::max(occ, 1)) / gx, (n + kGJ - 1) / kGJ));
+        const dim3 gu(gx, gy), gp(gx, kGJ / kGJPanelK);
         for (int K = 0; K < n; K += kGJ) {
             const int bb = std::min(kGJ, n - K);
             k_gj_pivot<<<1, 256, 0, s>>>(n, K, bb, Ad.p, Dinv.p, bad.p); ::bd::note_launch();
-            k_gj_panel<<<(n + 127) / 128, 128, 0, s>>>(n, K, bb, Ad.p, Dinv.p, W.p, Cb.p); ::bd::note_launch();
+            k_gj_panel<<<gp, 128, 0, s>>>(n, K, bb, Ad.p, Dinv.p, W.p, Cb.p); ::bd::note_launch();
             k_gj_update<<<gu, 128, 0, s>>>(n, K, bb, Ad.p, Dinv.p, W.p, Cb.p); ::bd::note_launch();
         }
         BD_LAUNCH_CHECK();
