@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "amg_bsr.cuh"
@@ -37,11 +38,11 @@ enum {
 };
 
 // node -> member, and each member's Chebyshev coefficients on one level:
-// coef[3k] = 1/theta, coef[3k+1] = c1, coef[3k+2] = c2
+// coef[4k] = 1/theta, coef[4k+1] = c1, coef[4k+2] = c2, coef[4k+3] = 1 + c1
 struct StCoef {
     const int *__restrict__ mem;
     const double *__restrict__ coef;
-    __device__ __forceinline__ const double *at(int p) const { return coef + 3 * mem[p]; }
+    __device__ __forceinline__ const double *at(int p) const { return coef + 4 * mem[p]; }
 };
 
 template <class S> struct StGather {
@@ -137,12 +138,80 @@ struct StStore {  // q = A p (FP64, PCG)
     __device__ __forceinline__ void operator()(int p, double y0, double y1) const { q[p] = make_double2(y0, y1); }
 };
 
+// The FP64 finest level's steps with the vectors its operator gathers (d0, u,
+// d, w) kept in (v + u, u) form and the inverse diagonal scaled per member
+// (idc2 = c2 D^{-1}, idt = D^{-1} / theta), as the single hierarchy's FP64
+// finest level does them: 2 FMA per stored node pair instead of 3 operations.
+// Pre-smoothing from zero with m = idc2 (f - A d0): u_s = (1 + c1) d0_s + (m_v
+// + m_u), u_u = (1 + c1) d0_u + m_u.
+struct StPreX {
+    const double2 *__restrict__ f;
+    const double2 *__restrict__ idc2;
+    const double2 *__restrict__ d0;  // (v + u, u)
+    double2 *__restrict__ u;         // (v + u, u)
+    StCoef c;
+    __device__ __forceinline__ void operator()(int p, double y0, double y1) const
+    {
+        const double c1p = c.at(p)[3];
+        const double2 fp = f[p], k = idc2[p], dp = d0[p];
+        const double m0 = k.x * (fp.x - y0), m1 = k.y * (fp.y - y1);
+        u[p] = make_double2(fma(c1p, dp.x, m0 + m1), fma(c1p, dp.y, m1));
+    }
+};
+struct StAddX {  // u += P e_c with u in (v + u, u) form
+    double2 *__restrict__ u;
+    __device__ __forceinline__ void operator()(int p, double y0, double y1) const
+    {
+        const double2 a = u[p];
+        u[p] = make_double2(a.x + (y0 + y1), a.y + y1);
+    }
+};
+// r = f - A u (plain), d = D^{-1} r / theta and w = u + d in (v + u, u) form
+struct StPost1X {
+    const double2 *__restrict__ f;
+    const double2 *__restrict__ idt;
+    const double2 *__restrict__ u;  // (v + u, u)
+    double2 *__restrict__ r;
+    double2 *__restrict__ d;
+    double2 *__restrict__ w;
+    __device__ __forceinline__ void operator()(int p, double y0, double y1) const
+    {
+        const double2 fp = f[p], k = idt[p], up = u[p];
+        const double r0 = fp.x - y0, r1 = fp.y - y1;
+        const double d1 = r1 * k.y, ds = r0 * k.x + d1;
+        r[p] = make_double2(r0, r1);
+        d[p] = make_double2(ds, d1);
+        w[p] = make_double2(up.x + ds, up.y + d1);
+    }
+};
+// u = w + (c1 d + c2 D^{-1} (r - A d)) in plain (v, u) form (the V-cycle's
+// output) from w and d in (v + u, u) form
+struct StPost2X {
+    const double2 *__restrict__ r;
+    const double2 *__restrict__ d;  // (v + u, u)
+    const double2 *__restrict__ idc2;
+    const double2 *__restrict__ w;  // (v + u, u)
+    double2 *__restrict__ u;
+    StCoef c;
+    __device__ __forceinline__ void operator()(int p, double y0, double y1) const
+    {
+        const double c1 = c.at(p)[1];
+        const double2 rp_ = r[p], dp = d[p], k = idc2[p], wp = w[p];
+        const double m0 = k.x * (rp_.x - y0), m1 = k.y * (rp_.y - y1);
+        const double uu = wp.y + fma(c1, dp.y, m1);
+        const double us = wp.x + fma(c1, dp.x, m0 + m1);
+        u[p] = make_double2(us - uu, uu);
+    }
+};
+
 // Finest level of the stack in sliced ELL with the shared Ki/Ke pattern of
 // the Bidomain operator (every member's own slices, its rows padded to whole
 // 32-row slices; padded rows, member -1, are skipped): one thread per row,
 // slot j of a slice holds entry j of its 32 rows; per node pair
 // a += Ki (v_q + u_q), b += Ke u_q, then y_v = c M_p v_p + a, y_u = a + b.
-template <class S, class E>
+// SU: the gathered vector is stored as (v + u, u), so a node pair costs two
+// FMAs and the row's own v is recovered once.
+template <class S, class E, bool SU = false>
 __global__ void __launch_bounds__(256) k_st_sell(int rows, const int *__restrict__ mem, const int *__restrict__ sptr,
                                                  const int *__restrict__ col, const v2<S> *__restrict__ kk,
                                                  const S *__restrict__ cm, StGather<S> g, E epi)
@@ -156,11 +225,11 @@ __global__ void __launch_bounds__(256) k_st_sell(int rows, const int *__restrict
             const size_t idx = (size_t)j * 32 + lane;
             const v2<S> k = kk[idx];
             const v2<S> x = g(col[idx]);
-            a = fma(k.x, x.x + x.y, a);
+            a = fma(k.x, SU ? x.x : x.x + x.y, a);
             b = fma(k.y, x.y, b);
         }
         const v2<S> xp = g(p);
-        epi(p, fma(cm[p], xp.x, a), a + b);
+        epi(p, fma(cm[p], SU ? xp.x - xp.y : xp.x, a), a + b);
     }
 }
 
@@ -248,6 +317,8 @@ template <class S> struct StPcg {
     const v2<S> *u0, *invd0;
     StCoef c0;
     const int *mem;                // finest-level node -> member
+    int psu;                       // p stored as (v + u, u) (sliced-ELL finest level)
+    int dsu;                       // FP64 V-cycle: d0 stored as (v + u, u)
 };
 
 enum { R_FSTATS = 0, R_PROJF, R_INIT, R_ZSTATS, R_PQ, R_XR, R_TRUE };
@@ -261,7 +332,8 @@ __device__ __forceinline__ void st_vin(const StPcg<S> &v, int i, double2 ri)
     if (sizeof(S) == 4) v.f0[i] = V2<S>::mk((S)ri.x, (S)ri.y);
     const v2<S> id = v.invd0[i];
     const S itS = (S)it;
-    v.d0[i] = V2<S>::mk((S)ri.x * id.x * itS, (S)ri.y * id.y * itS);
+    const S dv = (S)ri.x * id.x * itS, du = (S)ri.y * id.y * itS;
+    v.d0[i] = V2<S>::mk(v.dsu ? dv + du : dv, du);
 }
 
 // Per-member totals -> scalars (last block, one thread per member).  Returns
@@ -385,7 +457,8 @@ __global__ void __launch_bounds__(kStThreads) k_st_red(StRed R, StPcg<S> v)
         if (sc[T_ACTIVE] != 0.0)
             for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
                 const double2 p = v.p[i], q = v.q[i];
-                acc[0] += p.x * q.x + p.y * q.y;
+                const double pv = v.psu ? p.x - p.y : p.x;
+                acc[0] += pv * q.x + p.y * q.y;
             }
     } else if (MODE == R_XR) {
         if (sc[T_ACTIVE] != 0.0) {
@@ -393,7 +466,7 @@ __global__ void __launch_bounds__(kStThreads) k_st_red(StRed R, StPcg<S> v)
             for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
                 const double2 p = v.p[i], q = v.q[i];
                 double2 xi = v.x[i], ri = v.r[i];
-                xi.x += al * p.x;
+                xi.x += al * (v.psu ? p.x - p.y : p.x);
                 xi.y += al * p.y;
                 ri.x -= al * q.x;
                 ri.y -= al * q.y;
@@ -453,8 +526,9 @@ __global__ void __launch_bounds__(kStThreads) k_st_red(StRed R, StPcg<S> v)
     }
 }
 
-// z <- z - mean(z_u) e_u; p = z (first iteration) or z + beta p; the projected
-// z kept for the next flexible beta.  Members no longer iterating keep p.
+// z <- z - mean(z_u) e_u; p = z (first iteration) or z + beta p, stored in
+// (v + u, u) form when psu; the projected z kept for the next flexible beta.
+// Members no longer iterating keep p.
 template <class S>
 __global__ void k_st_p(int N, StPcg<S> v, const double *__restrict__ scal)
 {
@@ -467,12 +541,13 @@ __global__ void k_st_p(int N, StPcg<S> v, const double *__restrict__ scal)
         zi.y -= sc[T_MEANZ];
         v.z[i] = zi;
         if (v.zold) v.zold[i] = zi;
+        const double2 zs = v.psu ? make_double2(zi.x + zi.y, zi.y) : zi;
         if (sc[T_IT] == 0.0) {
-            v.p[i] = zi;
+            v.p[i] = zs;
         } else {
             const double beta = sc[T_BETA];
             const double2 pi = v.p[i];
-            v.p[i] = make_double2(zi.x + beta * pi.x, zi.y + beta * pi.y);
+            v.p[i] = make_double2(zs.x + beta * pi.x, zs.y + beta * pi.y);
         }
     }
 }
@@ -511,6 +586,10 @@ struct StLevel {
     DBuf<int> ssptr, scol;
     DBuf<double> skk, scm;     // FP64 (the PCG's A p always; the FP64 V-cycle)
     DBuf<float> skk32, scm32;  // FP32 V-cycle
+    // FP64 V-cycle on the sliced finest level: its gathered vectors in
+    // (v + u, u) form, with the members' c2 D^{-1} and D^{-1} / theta
+    bool su = false;
+    DBuf<double> idc2, idt;
 };
 
 }  // namespace bd
@@ -745,13 +824,14 @@ int st_create(amg_stack *b, cudaStream_t s)
         // node -> member (-1 on padding), Chebyshev coefficients, inverse diagonals
         BD_TRY(S.mem.alloc((size_t)std::max(S.N, 1)));
         BD_CUDA(cudaMemsetAsync(S.mem.p, 0xff, S.mem.bytes(), s));
-        std::vector<double> coef(3 * (size_t)count, 0.0);
+        std::vector<double> coef(4 * (size_t)count, 0.0);
         for (int k : order[l]) {
             const Level &Lk = b->h[k]->lev[l];
             k_st_fill<<<grid_for(Lk.N, 256), 256, 0, s>>>(Lk.N, S.mem.p + off[l][k], k); ::bd::note_launch();
-            coef[3 * k] = Lk.ch_inv_theta;
-            coef[3 * k + 1] = Lk.ch_c1;
-            coef[3 * k + 2] = Lk.ch_c2;
+            coef[4 * k] = Lk.ch_inv_theta;
+            coef[4 * k + 1] = Lk.ch_c1;
+            coef[4 * k + 2] = Lk.ch_c2;
+            coef[4 * k + 3] = 1.0 + Lk.ch_c1;
         }
         BD_TRY(S.coef.alloc(coef.size()));
         BD_CUDA(cudaMemcpyAsync(S.coef.p, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, s));
@@ -772,6 +852,25 @@ int st_create(amg_stack *b, cudaStream_t s)
             for (int k : order[l])
                 BD_CUDA(cudaMemcpyAsync(S.invd.p + 2 * off[l][k], b->h[k]->lev[l].invdiag.p,
                                         sizeof(double) * 2 * b->h[k]->lev[l].N, cudaMemcpyDeviceToDevice, s));
+            // the (v + u, u) form on a sliced finest level whose members all carry
+            // their scaled inverse diagonals (every FP64 sliced finest level does)
+            // (only the members that smooth there, rows [0, Ns), use them)
+            bool su = l == 0 && sell0;
+            for (int k : order[l])
+                if (b->nlev[k] > 1) su = su && b->h[k]->lev[0].idc2.p && b->h[k]->lev[0].idt.p;
+            S.su = su;
+            if (su) {
+                BD_TRY(st_vec(S.idc2, n2, s));
+                BD_TRY(st_vec(S.idt, n2, s));
+                for (int k : order[l]) {
+                    if (b->nlev[k] <= 1) continue;
+                    const size_t bytes = sizeof(double) * 2 * b->h[k]->lev[0].N;
+                    BD_CUDA(cudaMemcpyAsync(S.idc2.p + 2 * off[0][k], b->h[k]->lev[0].idc2.p, bytes,
+                                            cudaMemcpyDeviceToDevice, s));
+                    BD_CUDA(cudaMemcpyAsync(S.idt.p + 2 * off[0][k], b->h[k]->lev[0].idt.p, bytes,
+                                            cudaMemcpyDeviceToDevice, s));
+                }
+            }
             if (l > 0) BD_TRY(st_vec(S.f, n2, s));
             BD_TRY(st_vec(S.u, n2, s));
             BD_TRY(st_vec(S.r, n2, s));
@@ -877,19 +976,20 @@ template <> const float *st_cm<float>(const StLevel &Lv) { return Lv.scm32.p; }
 
 // Operator of stack level l on rows [0, rows): the finest level's sliced ELL
 // when built, block CSR otherwise.
-template <class S, class E>
+template <class S, class E, bool SU = false>
 int st_apply(const StLevel &Lv, int l, int rows, const S *vals, const v2<S> *x, E e, cudaStream_t s)
 {
     if (l == 0 && Lv.sell) {
         if (rows <= 0) return BD_OK;
         const int grid = (int)std::min<long long>(((long long)rows + 255) / 256, (long long)kSM * 8);
-        k_st_sell<S, E><<<grid, 256, 0, s>>>(rows, Lv.mem.p, Lv.ssptr.p, Lv.scol.p, st_kk<S>(Lv), st_cm<S>(Lv),
-                                             StGather<S>{x}, e);
+        k_st_sell<S, E, SU><<<grid, 256, 0, s>>>(rows, Lv.mem.p, Lv.ssptr.p, Lv.scol.p, st_kk<S>(Lv), st_cm<S>(Lv),
+                                                 StGather<S>{x}, e);
         ::bd::note_launch();
         BD_LAUNCH_CHECK();
         return BD_OK;
     }
-    return launch_bsr_rows<S>(rows, Lv.A.rp.p, Lv.A.ci.p, vals, Lv.lanes[0], StGather<S>{x}, e, s);
+    if constexpr (SU) return BD_ESTATE;  // the (v + u, u) form exists on the sliced level only
+    else return launch_bsr_rows<S>(rows, Lv.A.rp.p, Lv.A.ci.p, vals, Lv.lanes[0], StGather<S>{x}, e, s);
 }
 
 template <class S>
@@ -901,6 +1001,16 @@ int st_vcycle(amg_stack *b, cudaStream_t s)
         if (Lv.Ns <= 0) continue;
         const StView<S> v = st_view<S>(b, l), cv = st_view<S>(b, l + 1);
         const StCoef c{Lv.mem.p, Lv.coef.p}, cc{b->lev[l + 1].mem.p, b->lev[l + 1].coef.p};
+        if constexpr (std::is_same<S, double>::value) {
+            if (l == 0 && Lv.su) {
+                BD_TRY((st_apply<S, StPreX, true>(Lv, l, Lv.Ns, v.Av, v.d,
+                                                  StPreX{v.f, (const double2 *)Lv.idc2.p, v.d, v.u, c}, s)));
+                BD_TRY((st_apply<S, StResid<S>, true>(Lv, l, Lv.Ns, v.Av, v.u, StResid<S>{v.f, v.r}, s)));
+                BD_TRY(launch_bsr<S>(Lv.R, v.Rv, Lv.lanes[1], StGather<S>{v.r},
+                                     StStoreD0<S>{cv.f, cv.d, cv.invd, cc}, s));
+                continue;
+            }
+        }
         BD_TRY(st_apply<S>(Lv, l, Lv.Ns, v.Av, v.d, StPre<S>{v.f, v.invd, v.d, v.u, c}, s));
         BD_TRY(st_apply<S>(Lv, l, Lv.Ns, v.Av, v.u, StResid<S>{v.f, v.r}, s));
         BD_TRY(launch_bsr<S>(Lv.R, v.Rv, Lv.lanes[1], StGather<S>{v.r}, StStoreD0<S>{cv.f, cv.d, cv.invd, cc}, s));
@@ -921,6 +1031,18 @@ int st_vcycle(amg_stack *b, cudaStream_t s)
         if (Lv.Ns <= 0) continue;
         const StView<S> v = st_view<S>(b, l), cv = st_view<S>(b, l + 1);
         const StCoef c{Lv.mem.p, Lv.coef.p};
+        if constexpr (std::is_same<S, double>::value) {
+            if (l == 0 && Lv.su) {
+                BD_TRY(launch_bsr<S>(Lv.P, v.Pv, Lv.lanes[2], StGather<S>{cv.u}, StAddX{v.u}, s));
+                BD_TRY((st_apply<S, StPost1X, true>(Lv, l, Lv.Ns, v.Av, v.u,
+                                                    StPost1X{v.f, (const double2 *)Lv.idt.p, v.u, v.r, v.d, v.w},
+                                                    s)));
+                BD_TRY((st_apply<S, StPost2X, true>(Lv, l, Lv.Ns, v.Av, v.d,
+                                                    StPost2X{v.r, v.d, (const double2 *)Lv.idc2.p, v.w, v.u, c},
+                                                    s)));
+                continue;
+            }
+        }
         BD_TRY(launch_bsr<S>(Lv.P, v.Pv, Lv.lanes[2], StGather<S>{cv.u}, StAdd<S>{v.u}, s));
         BD_TRY(st_apply<S>(Lv, l, Lv.Ns, v.Av, v.u, StPost1<S>{v.f, v.invd, v.u, v.r, v.d, v.w, c}, s));
         BD_TRY(st_apply<S>(Lv, l, Lv.Ns, v.Av, v.d, StPost2<S>{v.r, v.d, v.invd, v.w, v.u, c}, s));
@@ -948,6 +1070,8 @@ StPcg<S> st_pcg(amg_stack *b)
     v.invd0 = v0.invd;
     v.c0 = StCoef{b->lev[0].mem.p, b->lev[0].coef.p};
     v.mem = b->lev[0].mem.p;
+    v.psu = b->lev[0].sell ? 1 : 0;
+    v.dsu = b->lev[0].su ? 1 : 0;
     return v;
 }
 
@@ -957,9 +1081,12 @@ StRed st_red(amg_stack *b, cudaGraphConditionalHandle cond)
             b->count, b->p32 ? 1 : 0, cond};
 }
 
-int st_apply_a(amg_stack *b, const double2 *x, double2 *q, cudaStream_t s)
+// q = A x on the finest level; su: x is stored in (v + u, u) form (the PCG's p
+// on a sliced level)
+int st_apply_a(amg_stack *b, const double2 *x, double2 *q, cudaStream_t s, bool su = false)
 {
     StLevel &S = b->lev[0];
+    if (S.sell && su) return st_apply<double, StStore, true>(S, 0, S.N, nullptr, x, StStore{q}, s);
     if (S.sell) return st_apply<double>(S, 0, S.N, nullptr, x, StStore{q}, s);
     return launch_bsr_rows<double>(S.N, S.A.rp.p, S.A.ci.p, S.A.v.p, lanes_for(S.A, false), StGather<double>{x},
                                    StStore{q}, s);
@@ -1008,7 +1135,7 @@ int st_capture(amg_stack *b)
     BD_TRY(st_vcycle<S>(b, s2));
     k_st_red<R_ZSTATS, S><<<nch, kStThreads, 0, s2>>>(st_red(b, 0), v); ::bd::note_launch();
     k_st_p<S><<<vg, kStThreads, 0, s2>>>(N0, v, b->scal.p); ::bd::note_launch();
-    BD_TRY(st_apply_a(b, v.p, v.q, s2));
+    BD_TRY(st_apply_a(b, v.p, v.q, s2, v.psu != 0));
     k_st_red<R_PQ, S><<<nch, kStThreads, 0, s2>>>(st_red(b, 0), v); ::bd::note_launch();
     k_st_red<R_XR, S><<<nch, kStThreads, 0, s2>>>(st_red(b, cond), v); ::bd::note_launch();
     BD_LAUNCH_CHECK();
