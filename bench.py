@@ -223,6 +223,61 @@ def recorded_traffic(fp32: bool = False):
         return None
 
 
+# Vector streams of one application of a coarse-level operator by V-cycle
+# step (the gathered vector counted once): pre-smoother f, D^-1, d0, u;
+# residual u, f, r; post-smoother halves u, f, D^-1, r, d, w and d, r, D^-1,
+# w, u.  Restriction and prolongation are counted separately below.
+COARSE_A_STREAMS = {"pre": 4, "residual": 3, "post1": 6, "post2": 5}
+
+
+def coarse_levels_roofline(B, h, bd_, its, hbm_peak, fp32):
+    """Roofline entries of the coarse-level operators (block CSR or sliced
+    block form; levels >= 1 for A, every level for R and P): algorithmic bytes
+    per launch (per 2x2 block 4 values and a 4-byte column, 4 bytes of row
+    offset per row, the V-cycle step's vector streams), FP64 operations per
+    launch (4 FMA per block; the epilogues' few per row not counted; none in
+    the FP32 V-cycle) and the event-timed mean per launch from the per-step
+    breakdown (one launch per step and PCG iteration)."""
+    val = 4 if fp32 else 8
+    vec = 2 * val
+    nl = B.amg_num_levels(h)
+    info = [B.amg_level_info(h, l) for l in range(nl)]
+    out = []
+
+    def entry(name, us, rows, blocks, nbytes):
+        ops = 0.0 if fp32 else 4.0 * blocks
+        t_hbm = nbytes / (hbm_peak * 1e9)
+        t_alu = ops / FP64_OPS_PEAK
+        bound = "alu" if t_alu > t_hbm else "hbm"
+        return {"op": name, "rows": rows, "blocks": blocks, "us_per_launch": us,
+                "algorithmic_bytes": nbytes, "fp64_ops": ops,
+                "hbm_gbs": nbytes / (us * 1e-6) / 1e9, "hbm_frac": t_hbm / (us * 1e-6),
+                "fp64_pipe_frac": t_alu / (us * 1e-6) if ops else None,
+                "bound": bound, "frac": max(t_hbm, t_alu) / (us * 1e-6)}
+
+    for l in range(nl - 1):
+        rows, rows_c = info[l]["n"] // 2, info[l + 1]["n"] // 2
+        pb = info[l]["p_nnz"] // 4
+        mat_p = (4 * val + 4) * pb
+        if l >= 1:
+            nb = info[l]["nnz"] // 4
+            mat = (4 * val + 4) * nb + 4 * (rows + 1)
+            us = [bd_.get(f"L{l}_{k}") for k in COARSE_A_STREAMS]
+            if all(u is not None for u in us):
+                nbytes = statistics.mean(mat + COARSE_A_STREAMS[k] * vec * rows for k in COARSE_A_STREAMS)
+                out.append(entry(f"A{l} (4 smoothing launches)", 1e3 * sum(bd_[f"L{l}_{k}"][0] for k in
+                                 COARSE_A_STREAMS) / (4 * its), rows, nb, nbytes))
+        r = bd_.get(f"L{l}_restrict")
+        if r:
+            out.append(entry(f"R{l}", 1e3 * r[0] / its, rows_c, pb,
+                             mat_p + 4 * (rows_c + 1) + vec * rows + 3 * vec * rows_c))
+        pp = bd_.get(f"L{l}_prolong")
+        if pp:
+            out.append(entry(f"P{l}", 1e3 * pp[0] / its, rows, pb,
+                             mat_p + 4 * (rows + 1) + vec * rows_c + 2 * vec * rows))
+    return out
+
+
 def amg_opts(B, args):
     over = {}
     if args.square_levels is not None:
@@ -387,6 +442,7 @@ def run_ours(args):
     # untimed: per-step device time of the solve phase (host-driven loop with
     # CUDA events around every step), per PCG iteration
     breakdown = None
+    coarse_roof = None
     if rank == 0:
         sysh = B.bd_assemble(mesh, p, fib_d, stream=stream)
         h = B.amg_setup(sysh, amg_opts(B, args), stream=stream)
@@ -398,6 +454,9 @@ def run_ours(args):
         bd_ = B.amg_profile_breakdown(h)
         breakdown = {k: round(1e3 * v[0] / its, 2) for k, v in
                      sorted(bd_.items(), key=lambda kv: -kv[1][0])}
+        pk = measured_peaks()
+        coarse_roof = coarse_levels_roofline(B, h, bd_, its, pk["hbm_gbs"] if pk else 6800.0,
+                                             args.precision == "fp32")
         sim.close()
         h.close()
         sysh.close()
@@ -493,6 +552,7 @@ def run_ours(args):
                    "levels": rec.get("levels"), "operator_complexity": rec.get("op_complexity"),
                    "lanes_A_R_P": rec.get("lanes"),
                    "breakdown_us_per_pcg_iteration": breakdown,
+                   "coarse_levels_roofline": coarse_roof,
                    "forms": forms,
                    "amg_options": {k: getattr(amg_opts(B, args), k) for k in
                                    ("theta", "square_levels", "coarse_eq_limit", "cheb_degree",

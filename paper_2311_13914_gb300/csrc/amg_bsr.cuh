@@ -36,6 +36,27 @@ static __device__ __forceinline__ BlkS<float> load_blk(const float *__restrict__
     return {p.x, p.y, p.z, p.w};
 }
 
+// ------------------------------------------------------------------ lane sums
+// Sums of y0 and y1 over the T lanes of a group, left in the group's first
+// lane (the other lanes hold partial values).  The lower half of the group
+// reduces y0 and the upper half y1, each in the tree an xor butterfly uses
+// (IEEE addition is commutative, so the results carry the butterfly's bits),
+// then y1 moves to the first lane: log2(T) adds per lane instead of 2 log2(T),
+// and FP64 adds are scarce on this part.
+template <int T, class S>
+static __device__ __forceinline__ void group_sum2(S &y0, S &y1)
+{
+    if constexpr (T > 1) {
+        const bool hi = (threadIdx.x & (T - 1)) >= T / 2;
+        S mine = hi ? y1 : y0;
+        mine += __shfl_xor_sync(0xffffffffu, hi ? y0 : y1, T / 2, T);
+#pragma unroll
+        for (int o = T / 4; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o, T);
+        y0 = mine;
+        y1 = __shfl_down_sync(0xffffffffu, mine, T / 2, T);
+    }
+}
+
 // ------------------------------------------------------------------ block-CSR SpMV
 // T lanes cooperate on one 2x2 block row (T = 1: one thread per row, no
 // reduction).  The row loop is warp-uniform so every lane reaches the shuffles.
@@ -61,11 +82,7 @@ static __global__ void __launch_bounds__(256) k_bsr(int N, const int *__restrict
             y0 = fma(a.a00, x.x, fma(a.a01, x.y, y0));
             y1 = fma(a.a10, x.x, fma(a.a11, x.y, y1));
         }
-#pragma unroll
-        for (int o = T / 2; o > 0; o >>= 1) {
-            y0 += __shfl_xor_sync(0xffffffffu, y0, o, T);
-            y1 += __shfl_xor_sync(0xffffffffu, y1, o, T);
-        }
+        group_sum2<T>(y0, y1);
         if (act && lane == 0) epi(p, y0, y1);
     }
 }
@@ -90,11 +107,7 @@ static __global__ void __launch_bounds__(TB) k_bsr_wide(int N, const int *__rest
             y0 = fma(a.a00, x.x, fma(a.a01, x.y, y0));
             y1 = fma(a.a10, x.x, fma(a.a11, x.y, y1));
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            y0 += __shfl_xor_sync(0xffffffffu, y0, o);
-            y1 += __shfl_xor_sync(0xffffffffu, y1, o);
-        }
+        group_sum2<32>(y0, y1);
         const int w = threadIdx.x >> 5;
         if ((threadIdx.x & 31) == 0) {
             red[0][w] = y0;

@@ -37,8 +37,8 @@ __device__ __forceinline__ BlkS<float> load_sliced(const float *__restrict__ v, 
 
 // One warp per slice of 32/K rows with K lanes each; warp w takes slices
 // [wsl[w], wsl[w+1]), which split the groups evenly over the warps.  Lane k of
-// a row sums entries k, k+K, ... and the K partial sums meet in a butterfly,
-// the order k_bsr<K> uses, so both forms give the same bits.  Rows sorted by
+// a row sums entries k, k+K, ... and the K partial sums meet in the lane-sum
+// tree k_bsr<K> uses (group_sum2), so both forms give the same bits.  Rows sorted by
 // length leave few padded positions, and every FP64 instruction of the loop
 // and the epilogue works on 32 lanes (the FP64 pipe, not HBM, bounds the
 // coarse levels in FP64).
@@ -62,11 +62,7 @@ __global__ void __launch_bounds__(256, MINB) k_bsell(const int *__restrict__ spt
             y0 = fma(a.a00, x.x, fma(a.a01, x.y, y0));
             y1 = fma(a.a10, x.x, fma(a.a11, x.y, y1));
         }
-#pragma unroll
-        for (int o = K / 2; o > 0; o >>= 1) {
-            y0 += __shfl_xor_sync(0xffffffffu, y0, o, K);
-            y1 += __shfl_xor_sync(0xffffffffu, y1, o, K);
-        }
+        group_sum2<K>(y0, y1);
         if ((lane & (K - 1)) == 0) {
             const int r = order[sl * (32 / K) + lane / K];
             if (r >= 0) epi(r, y0, y1);
@@ -1347,11 +1343,7 @@ __global__ void __launch_bounds__(256) k_bsr_reduce(int N, const int *__restrict
             y0 = fma(a.a00, xq.x, fma(a.a01, xq.y, y0));
             y1 = fma(a.a10, xq.x, fma(a.a11, xq.y, y1));
         }
-#pragma unroll
-        for (int o = T / 2; o > 0; o >>= 1) {
-            y0 += __shfl_xor_sync(0xffffffffu, y0, o, T);
-            y1 += __shfl_xor_sync(0xffffffffu, y1, o, T);
-        }
+        group_sum2<T>(y0, y1);
         if (act && lane == 0) {
             const double2 xp = x[p];
             if (MODE == 0) {
