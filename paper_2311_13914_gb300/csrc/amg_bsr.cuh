@@ -87,6 +87,38 @@ static __global__ void __launch_bounds__(256) k_bsr(int N, const int *__restrict
     }
 }
 
+// The same rows in equal contiguous shares, one thread block per SM (rows
+// [N b / G, N (b + 1) / G) for block b of G): for operators whose row groups
+// fit one wave, so that no SM runs a block more than the others.
+template <int T, class S, class G, class E>
+static __global__ void __launch_bounds__(1024) k_bsr_eq(int N, const int *__restrict__ rp,
+                                                  const int *__restrict__ ci, const S *__restrict__ v,
+                                                  G gather, E epi)
+{
+    const int r0 = (int)((long long)N * blockIdx.x / gridDim.x);
+    const int r1 = (int)((long long)N * (blockIdx.x + 1) / gridDim.x);
+    const int lane = threadIdx.x & (T - 1);
+    const int groups = blockDim.x / T;
+    const int warp_first = (threadIdx.x & ~31) / T;
+    const int g_in_warp = (threadIdx.x & 31) / T;
+    for (int pw = r0 + warp_first; pw < r1; pw += groups) {
+        const int p = pw + g_in_warp;
+        const bool act = p < r1;
+        S y0 = 0, y1 = 0;
+        const int e = act ? rp[p + 1] : 0;
+#pragma unroll 4
+        for (int t = act ? rp[p] + lane : 0; t < e; t += T) {
+            const int q = ci[t];
+            const BlkS<S> a = load_blk(v, (size_t)t);
+            const v2<S> x = gather(q);
+            y0 = fma(a.a00, x.x, fma(a.a01, x.y, y0));
+            y1 = fma(a.a10, x.x, fma(a.a11, x.y, y1));
+        }
+        group_sum2<T>(y0, y1);
+        if (act && lane == 0) epi(p, y0, y1);
+    }
+}
+
 // Long rows on small levels (few hundred to a few thousand block rows of
 // hundreds of blocks): a whole thread block of TB threads per row, so that each
 // thread walks only a few blocks; warp shuffles then shared memory reduce.
@@ -143,6 +175,23 @@ static int launch_bsr_rows(int N, const int *rp, const int *ci, const S *vals, i
         case 128: k_bsr_wide<128, S><<<gw, 128, 0, s>>>(N, rp, ci, vals, g, e); ::bd::note_launch(); break;
         default: k_bsr_wide<256, S><<<gw, 256, 0, s>>>(N, rp, ci, vals, g, e); ::bd::note_launch(); break;
         }
+        BD_LAUNCH_CHECK();
+        return BD_OK;
+    }
+    if ((long long)N * T <= (long long)kSM * 1024) {
+        // one block per SM, equal shares of the rows
+        const long long per = ((long long)N + kSM - 1) / kSM * T;
+        const int tb = (int)std::min<long long>(1024, std::max<long long>(32, (per + 31) / 32 * 32));
+        const int gb = (int)std::min<long long>(kSM, N);
+        switch (T) {
+        case 1: k_bsr_eq<1, S><<<gb, tb, 0, s>>>(N, rp, ci, vals, g, e); break;
+        case 2: k_bsr_eq<2, S><<<gb, tb, 0, s>>>(N, rp, ci, vals, g, e); break;
+        case 4: k_bsr_eq<4, S><<<gb, tb, 0, s>>>(N, rp, ci, vals, g, e); break;
+        case 8: k_bsr_eq<8, S><<<gb, tb, 0, s>>>(N, rp, ci, vals, g, e); break;
+        case 16: k_bsr_eq<16, S><<<gb, tb, 0, s>>>(N, rp, ci, vals, g, e); break;
+        default: k_bsr_eq<32, S><<<gb, tb, 0, s>>>(N, rp, ci, vals, g, e); break;
+        }
+        ::bd::note_launch();
         BD_LAUNCH_CHECK();
         return BD_OK;
     }
