@@ -438,6 +438,12 @@ def run_ours(args):
             forms["batch"] = {prec: batch_measure(ab, prec, args.form_steps, 2, stream)
                               for prec in ("fp64", "fp32")}
             forms["serve"] = serve_measure(ab, "fp32", args.requests)
+            sa = argparse.Namespace(**{**vars(args), "mode": "sweep", "coarse_eq_limit": None,
+                                       "autotune": 1, "precision": "fp64"})
+            ck = ClockSampler(local)
+            ck.start()
+            forms["theta_sweep"] = sweep_measure(sa, SWEEP_FORM_STEPS, stream, mesh, fib, stim)
+            forms["theta_sweep"]["clocks"] = ck.stop()
 
     # untimed: per-step device time of the solve phase (host-driven loop with
     # CUDA events around every step), per PCG iteration
@@ -902,24 +908,18 @@ def run_batch(args):
             "clocks": r["clocks"]}
 
 
-def run_sweep(args):
+def sweep_measure(args, T, stream, mesh, fib, stim):
     """Strength threshold sweep (the analogue of the paper's threshold
     calibration, Section 6.1): for each theta, the coupled scheme (block AMG-PCG
     per step) and the paper's decoupled scheme (elliptic AMG-PCG + parabolic
-    Jacobi-CG per step), --time-steps steps each from rest with the corner
-    stimulus; hierarchy sizes, setup time, iterations and device solve time."""
+    Jacobi-CG per step), T steps each from rest with the corner stimulus;
+    hierarchy sizes, setup time, iterations and device solve time."""
     import torch
 
     from paper_2311_13914_gb300 import binding as B
     from paper_2311_13914_gb300 import workloads as W
 
-    rank, local, world = dist_info()
-    torch.cuda.set_device(local)
-    B.lib()
-    mesh, fib, stim, _ = workload(args.workload)
     p = W.DEFAULT_PARAMS
-    T = args.time_steps
-    stream = torch.cuda.Stream()
     sysh = B.bd_assemble(mesh, p, torch.tensor(fib.reshape(-1), device="cuda"), stream=stream)
     stim_d = torch.tensor(stim, device="cuda")
     rows = []
@@ -964,15 +964,30 @@ def run_sweep(args):
             h.close()
             row[scheme] = r
         rows.append(row)
-    ref = next(r for r in rows if r["theta"] == 0.06)
+    sysh.close()
+    return {"workload": f"{mesh['nx']}x{mesh['ny']}x{mesh['nz']} slab, {T} time steps from rest, "
+                        f"corner stimulus; decoupled parabolic solve Jacobi-CG",
+            "timing": "CUDA events (setup) and the library's per-solve device time", "sweep": rows}
+
+
+def run_sweep(args):
+    import torch
+
+    from paper_2311_13914_gb300 import binding as B
+
+    rank, local, world = dist_info()
+    torch.cuda.set_device(local)
+    B.lib()
+    mesh, fib, stim, _ = workload(args.workload)
+    r = sweep_measure(args, args.time_steps, torch.cuda.Stream(), mesh, fib, stim)
+    ref = next(x for x in r["sweep"] if x["theta"] == 0.06)
     return {"metric": "strength-threshold sweep: AMG-PCG iterations and device time per time step",
             "value": 1e3 / ref["coupled"]["solve_ms_per_step"], "unit": "solves/s (coupled, theta 0.06)",
             "n_gpus": 1, "higher_is_better": True, "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{mesh['nx']}x{mesh['ny']}x{mesh['nz']} slab, {T} time steps from rest, "
-                                   f"corner stimulus; decoupled parabolic solve Jacobi-CG",
-                       "sweep": rows}}
+            "config": {"workload": r["workload"], "sweep": r["sweep"]}}
 
 
+SWEEP_FORM_STEPS = 20  # time steps per theta and scheme of the sweep in the default line
 STEP_COARSE_EQ_LIMIT = 2000  # time-stepping mode's coarsest level (see --coarse-eq-limit)
 
 

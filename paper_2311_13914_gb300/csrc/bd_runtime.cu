@@ -221,40 +221,60 @@ int sort_segments(int *keys, int *payload, const int *seg, int nseg, int max_len
 // Each rounded product is split into three 32-bit digits and added with
 // 64-bit integer atomics (associative, so the result does not depend on the
 // order of the additions).
-__device__ __forceinline__ void exact_acc_add(long long *acc, double x, int *flags)
+
+// Digits of a finite double: limb index li and three signed 32-bit digits
+// (two's complement in 64 bits) such that x = sum_k d_k 2^(32 (li + k) - 1074).
+// Returns false for an infinity or NaN (flag bits in *nf: 1 NaN, 2 +inf, 4 -inf).
+__device__ __forceinline__ bool exact_digits(double x, int &li, unsigned long long &d0, unsigned long long &d1,
+                                             unsigned long long &d2, int &nf)
 {
     unsigned long long b = (unsigned long long)__double_as_longlong(x);
     int neg = (int)(b >> 63);
     int E = (int)((b >> 52) & 0x7ff);
     unsigned long long m = b & 0xFFFFFFFFFFFFFULL;
+    li = 0;
+    d0 = d1 = d2 = 0;
+    nf = 0;
     if (E == 0x7ff) {
-        atomicOr(flags, m ? 1 : (neg ? 4 : 2));
-        return;
+        nf = m ? 1 : (neg ? 4 : 2);
+        return false;
     }
     int off = 0;
     if (E != 0) {
         m |= (1ULL << 52);
         off = E - 1;
     }
-    if (m == 0) return;
-    int li = off >> 5, sh = off & 31;
+    if (m == 0) return true;
+    li = off >> 5;
+    const int sh = off & 31;
     unsigned long long t0 = (m & 0xffffffffULL) << sh;
     unsigned long long t1 = (m >> 32) << sh;
-    unsigned long long d0 = t0 & 0xffffffffULL;
+    d0 = t0 & 0xffffffffULL;
     unsigned long long u1 = (t0 >> 32) + (t1 & 0xffffffffULL);
-    unsigned long long d1 = u1 & 0xffffffffULL;
-    unsigned long long d2 = (u1 >> 32) + (t1 >> 32);
+    d1 = u1 & 0xffffffffULL;
+    d2 = (u1 >> 32) + (t1 >> 32);
     if (neg) {
         d0 = 0ULL - d0;
         d1 = 0ULL - d1;
         d2 = 0ULL - d2;
     }
+    return true;
+}
+
+__device__ __forceinline__ void exact_acc_digits(long long *acc, int li, unsigned long long d0,
+                                                 unsigned long long d1, unsigned long long d2)
+{
     unsigned long long *a = (unsigned long long *)acc;
     if (d0) atomicAdd(a + li, d0);
     if (d1) atomicAdd(a + li + 1, d1);
     if (d2) atomicAdd(a + li + 2, d2);
 }
 
+// Whole warps step through the elements.  When every nonzero finite product
+// of a warp's step falls on the same limb index (the usual case: products of
+// similar magnitude), the warp sums its digits exactly (32 signed 33-bit
+// digits fit 64 bits) and one lane adds them; otherwise every lane adds its
+// own.  Integer sums are associative, so the total is the same either way.
 __global__ void k_exact_dot_partial(const double *__restrict__ x, const double *__restrict__ y,
                                     int n, long long *gacc)
 {
@@ -263,9 +283,31 @@ __global__ void k_exact_dot_partial(const double *__restrict__ x, const double *
     for (int i = threadIdx.x; i < kExactLimbs; i += blockDim.x) acc[i] = 0;
     if (threadIdx.x == 0) flags = 0;
     __syncthreads();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double p = __dmul_rn(x[i], y[i]);
-        exact_acc_add(acc, p, &flags);
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const long long i = base + lane;
+        const double p = i < n ? __dmul_rn(x[i], y[i]) : 0.0;
+        int li, nf;
+        unsigned long long d0, d1, d2;
+        const bool fin = exact_digits(p, li, d0, d1, d2, nf);
+        const bool nz = fin && (d0 | d1 | d2);
+        const unsigned nzm = __ballot_sync(0xffffffffu, nz);
+        const bool allfin = __all_sync(0xffffffffu, fin);
+        if (nzm == 0 && allfin) continue;
+        const int li0 = __shfl_sync(0xffffffffu, li, __ffs(nzm ? nzm : 1u) - 1);
+        if (allfin && __all_sync(0xffffffffu, !nz || li == li0)) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+                d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+                d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+            }
+            if (lane == 0) exact_acc_digits(acc, li0, d0, d1, d2);
+        } else {
+            if (!fin) atomicOr(&flags, nf);
+            else if (nz) exact_acc_digits(acc, li, d0, d1, d2);
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kExactLimbs; i += blockDim.x)

@@ -49,7 +49,8 @@ def _same(a: sp.csr_matrix, b: sp.csr_matrix):
 
 def test_reproducible_dot_bit_exact(B, oracle_lib):
     """The device long-accumulator dot equals the oracle's correctly rounded
-    dot bit for bit, on cancelling, wide-range, subnormal and ragged inputs."""
+    dot bit for bit, on cancelling, wide-range, subnormal, sparse, constant
+    and ragged inputs."""
     import torch
 
     rng = np.random.default_rng(12)
@@ -60,6 +61,10 @@ def test_reproducible_dot_bit_exact(B, oracle_lib):
         (np.array([1e300, 1.0, -1e300, 3e-310]), np.array([1.0, 1e-16, 1.0, 1.0])),
         (np.array([1.0, 2.0 ** -53]), np.array([1.0, 1.0])),
         (np.zeros(0), np.zeros(0)),
+        # half the products zero (lanes a warp's shared-limb sum skips), and a
+        # long run of equal negative products (warp sums at full width)
+        (rng.standard_normal(100003) * (rng.random(100003) < 0.5), rng.standard_normal(100003)),
+        (np.full(65571, -3.0), np.full(65571, 7.0 + 2.0 ** -40)),
     ]
     for x, y in cases:
         want = oracle_lib.dot_exact(x, y)
