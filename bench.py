@@ -230,6 +230,21 @@ def recorded_traffic(fp32: bool = False):
 COARSE_A_STREAMS = {"pre": 4, "residual": 3, "post1": 6, "post2": 5}
 
 
+def csr_equivalent(info, launch_s, hbm_peak, fp32):
+    """What a plain scalar-CSR SpMV of the finest operator would move per
+    application (per scalar nonzero a value and a 4-byte column, 4 bytes of row
+    offset per row, x read and y written once; FP64 values, or FP32 for the FP32
+    V-cycle), divided by the measured mean launch: the bandwidth the stored
+    format stands in for.  It can exceed the HBM peak."""
+    if not info or not launch_s:
+        return {}
+    val = 4 if fp32 else 8
+    n, nnz = info["n"], info["nnz"]
+    nbytes = (val + 4) * nnz + 4 * (n + 1) + 2 * val * n
+    return {"csr_equivalent_bytes_per_launch": nbytes, "csr_equivalent_gbs": nbytes / launch_s / 1e9,
+            "csr_equivalent_frac": nbytes / launch_s / 1e9 / hbm_peak}
+
+
 def coarse_levels_roofline(B, h, bd_, its, hbm_peak, fp32):
     """Roofline entries of the coarse-level operators (block CSR or sliced
     block form; levels >= 1 for A, every level for R and P): algorithmic bytes
@@ -449,6 +464,7 @@ def run_ours(args):
     # CUDA events around every step), per PCG iteration
     breakdown = None
     coarse_roof = None
+    fine_info = None
     if rank == 0:
         sysh = B.bd_assemble(mesh, p, fib_d, stream=stream)
         h = B.amg_setup(sysh, amg_opts(B, args), stream=stream)
@@ -463,6 +479,7 @@ def run_ours(args):
         pk = measured_peaks()
         coarse_roof = coarse_levels_roofline(B, h, bd_, its, pk["hbm_gbs"] if pk else 6800.0,
                                              args.precision == "fp32")
+        fine_info = B.amg_level_info(h, 0)
         sim.close()
         h.close()
         sysh.close()
@@ -541,6 +558,7 @@ def run_ours(args):
                  "fp64_tflops_frac": (achieved_tflops / (FP64_ALU_PEAK / 1e12)
                                       if achieved_tflops and not fp32 else None),
                  "floors_us": {"hbm": 1e6 * t_hbm / nl, "fp64_pipe": 1e6 * t_alu / nl},
+                 **csr_equivalent(fine_info, prof_s / nl if nl else None, hbm_peak, fp32),
                  "mean_launch_us": 1e3 * rec["prof_total_ms"] / nl})
     out = {
         "metric": "AMG-PCG solves/sec to rtol 1e-8 (coupled Bidomain, paper-size slab, time stepping)",

@@ -96,3 +96,15 @@ def test_coarse_levels_roofline_accounting():
     out32 = {e["op"]: e for e in bench.coarse_levels_roofline(_FakeLevels(), None, bd_, its, 1000.0, True)}
     assert out32["P0"]["fp64_ops"] == 0 and out32["P0"]["bound"] == "hbm"
     assert out32["P0"]["algorithmic_bytes"] == pytest.approx(20 * 3000 + 4 * 1001 + 8 * 100 + 2 * 8 * 1000)
+
+
+def test_csr_equivalent_bandwidth():
+    info = {"n": 1000, "nnz": 27000}
+    out = bench.csr_equivalent(info, 1e-6, 1000.0, False)
+    nbytes = 12 * 27000 + 4 * 1001 + 16 * 1000
+    assert out["csr_equivalent_bytes_per_launch"] == nbytes
+    assert out["csr_equivalent_gbs"] == pytest.approx(nbytes / 1e-6 / 1e9)
+    assert out["csr_equivalent_frac"] == pytest.approx(nbytes / 1e-6 / 1e9 / 1000.0)
+    assert bench.csr_equivalent(info, 1e-6, 1000.0, True)["csr_equivalent_bytes_per_launch"] == \
+        8 * 27000 + 4 * 1001 + 8 * 1000
+    assert bench.csr_equivalent(None, 1e-6, 1000.0, False) == {}
