@@ -78,34 +78,40 @@ __device__ __forceinline__ bool strength_w(const int *rp, const int *ci, const d
     return w >= theta;
 }
 
+// One pass forms every entry's weight (a square root and a division, costly
+// on the FP64 pipe) and counts the strong ones; wt[t] keeps the weight of a
+// strong entry and -1 otherwise (weights are >= 0), so the fill only compacts.
 __global__ void k_strength_count(int N, const int *__restrict__ rp, const int *__restrict__ ci,
                                  const double *__restrict__ v, const double *__restrict__ diag,
-                                 double theta, int *cnt)
+                                 double theta, int *cnt, double *__restrict__ wt)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
     int c = 0;
     double w;
-    for (int t = rp[p]; t < rp[p + 1]; t++)
-        if (strength_w(rp, ci, v, diag, p, t, theta, &w)) c++;
+    for (int t = rp[p]; t < rp[p + 1]; t++) {
+        const bool strong = strength_w(rp, ci, v, diag, p, t, theta, &w);
+        wt[t] = strong ? w : -1.0;
+        c += strong;
+    }
     cnt[p] = c;
 }
 
 __global__ void k_strength_fill(int N, const int *__restrict__ rp, const int *__restrict__ ci,
-                                const double *__restrict__ v, const double *__restrict__ diag,
-                                double theta, const int *__restrict__ srp, int *__restrict__ sci,
-                                double *__restrict__ sw)
+                                const double *__restrict__ wt, const int *__restrict__ srp,
+                                int *__restrict__ sci, double *__restrict__ sw)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
     int pos = srp[p];
-    double w;
-    for (int t = rp[p]; t < rp[p + 1]; t++)
-        if (strength_w(rp, ci, v, diag, p, t, theta, &w)) {
+    for (int t = rp[p]; t < rp[p + 1]; t++) {
+        const double w = wt[t];
+        if (w >= 0.0) {
             sci[pos] = ci[t];
             sw[pos] = w;
             pos++;
         }
+    }
 }
 
 // ------------------------------------------------------------------ deterministic SpGEMM
@@ -1346,18 +1352,20 @@ static int coarsen_level(amg_hierarchy *h, int l, bool &is_coarsest, cudaStream_
     CSR S;
     S.nr = S.nc = N;
     DBuf<int> cnt;
+    DBuf<double> wt;
     BD_TRY(cnt.alloc((size_t)N + 1));
+    BD_TRY(wt.alloc((size_t)L.A.nb));
     BD_TRY(S.rp.alloc((size_t)N + 1));
     k_strength_count<<<nblk(N, row_block(N)), row_block(N), 0, s>>>(N, L.A.rp.p, L.A.ci.p, L.A.v.p, diag.p, o.theta,
-                                                                   cnt.p); ::bd::note_launch();
+                                                                   cnt.p, wt.p); ::bd::note_launch();
     BD_LAUNCH_CHECK();
     long long snnz = 0;
     BD_TRY(exclusive_scan(cnt.p, S.rp.p, N, &snnz, s));
     S.nnz = snnz;
     BD_TRY(S.ci.alloc((size_t)snnz));
     BD_TRY(S.v.alloc((size_t)snnz));
-    k_strength_fill<<<nblk(N, row_block(N)), row_block(N), 0, s>>>(N, L.A.rp.p, L.A.ci.p, L.A.v.p, diag.p, o.theta, S.rp.p,
-                                            S.ci.p, S.v.p); ::bd::note_launch();
+    k_strength_fill<<<nblk(N, row_block(N)), row_block(N), 0, s>>>(N, L.A.rp.p, L.A.ci.p, wt.p, S.rp.p, S.ci.p,
+                                                                  S.v.p); ::bd::note_launch();
     BD_LAUNCH_CHECK();
     int hbad = 0;
     BD_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
