@@ -91,7 +91,7 @@ static __global__ void __launch_bounds__(256) k_bsr(int N, const int *__restrict
 // [N b / G, N (b + 1) / G) for block b of G): for operators whose row groups
 // fit one wave, so that no SM runs a block more than the others.
 template <int T, class S, class G, class E>
-static __global__ void __launch_bounds__(1024) k_bsr_eq(int N, const int *__restrict__ rp,
+static __global__ void __launch_bounds__(1024, 1) k_bsr_eq(int N, const int *__restrict__ rp,
                                                   const int *__restrict__ ci, const S *__restrict__ v,
                                                   G gather, E epi)
 {
