@@ -122,8 +122,10 @@ static __global__ void __launch_bounds__(1024, 1) k_bsr_eq(int N, const int *__r
 // Long rows on small levels (few hundred to a few thousand block rows of
 // hundreds of blocks): a whole thread block of TB threads per row, so that each
 // thread walks only a few blocks; warp shuffles then shared memory reduce.
+// The launch bound asks for 1024 resident threads per SM, not 2048, so that
+// the FP64 instantiations get 64 registers (at 32 they spill).
 template <int TB, class S, class G, class E>
-static __global__ void __launch_bounds__(TB) k_bsr_wide(int N, const int *__restrict__ rp,
+static __global__ void __launch_bounds__(TB, 1024 / TB) k_bsr_wide(int N, const int *__restrict__ rp,
                                                   const int *__restrict__ ci,
                                                   const S *__restrict__ v, G gather, E epi)
 {
