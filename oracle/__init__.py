@@ -8,13 +8,17 @@ shares no code with the CUDA path.  The arithmetic lives in ``bd_oracle.c``
 
 Every function follows a passage of arXiv 2311.13914 (cited in bd_oracle.c).
 Pins that tie it to the paper and to mathematics, not to itself, live in
-``tests/test_oracle_*.py``.  Parity status: assembly (including the fibre
-field sampled at the Gauss z-levels, against an independent quadrature),
-strength, the squared strength graph (against a dense (I + W)^2), MIS,
+``tests/test_oracle_*.py``.  Every function is pinned: assembly (closed-form
+stencils, patch test, second-order convergence, and the fibre field sampled at
+the Gauss z-levels against an independent quadrature), the correctly rounded
+dot, strength, the squared strength graph (against a dense (I + W)^2), MIS and
 aggregation (brute force on the plain and the squared graph), prolongators,
-Galerkin operators, eigen-estimate, smoother, coarse solve, V-cycle and PCG
-are pinned (closed forms, brute force, dense linear algebra); the comparison with the paper's own timings is "parity
-unpinned" because the paper prints no worked example for this system.
+Galerkin operators (dense triple product), eigen-estimate (closed-form 1-D
+Laplacian, dense bisection), smoother (closed-form error polynomial), coarse
+solve, V-cycle and PCG (dense pseudo-inverse), the time step (explicit Euler
+when space-clamped) and the decoupled scheme (dense solves).  The paper prints
+no worked example for this system, so no stored value comes from it; the
+stored 100-step and large-slab runs are written from this module alone.
 """
 from __future__ import annotations
 
