@@ -157,6 +157,15 @@ __global__ void k_slice_warps(int nsl, long long groups, int warps, const int *_
     wsl[w] = lo;
 }
 
+// Threads per block of the FP64 finest-level kernels: one block of 32 warps
+// per SM (measured against four blocks of 8 warps: 2-4 us shorter launches,
+// with the same warps resident and a quarter of the blocks to start and end),
+// where every SM then gets at least a slice per warp.  Smaller levels keep
+// blocks of 8 warps, so that small solves running side by side (graph branches,
+// served requests) share the SMs instead of each block holding one.
+constexpr int kFineTPB = 1024;
+static bool fine_wide(long long N) { return (N + 31) / 32 >= (long long)kSM * (kFineTPB / 32); }
+
 // ------------------------------------------------------------------ finest level, sliced ELL
 // Block b's share [share_lo(n), share_hi(n)) of n rows or nodes: the grid
 // splits the 32-row slices in equal contiguous parts, so with one resident
@@ -218,8 +227,8 @@ __device__ __forceinline__ void sell_row(int p, int lane, const int *__restrict_
     y1 = a + b;
 }
 
-template <class S, class G, class E, bool SU = false, int MINB = 8>
-__global__ void __launch_bounds__(256, MINB) k_sell(int N, const int *__restrict__ sptr,
+template <class S, class G, class E, bool SU = false, int MINB = 8, int TPB = 256>
+__global__ void __launch_bounds__(TPB, MINB) k_sell(int N, const int *__restrict__ sptr,
                                                const int *__restrict__ col,
                                                const unsigned char *__restrict__ code, Stencil st,
                                                const v2<S> *__restrict__ kk,
@@ -684,9 +693,16 @@ static int apply_level(amg_hierarchy *h, int l, const LV<S> &lv, G g, E e, cudaS
     const Level &L = h->lev[l];
     if (l == 0 && h->sell.valid) {
         const FineSell &F = h->sell;
-        constexpr int MB = sizeof(S) == 8 ? 4 : 8;  // FP64: fewer, deeper-pipelined threads
-        int grid = (int)std::min<long long>(((long long)L.N + 31) / 32, (long long)kSM * MB);
-        k_sell<S, G, E, SU, MB><<<grid, 256, 0, s>>>(L.N, F.sptr.p, F.col.p, F.code.p, stencil_of(F), lv.kk, lv.cm, g, e); ::bd::note_launch();
+        const long long slices = ((long long)L.N + 31) / 32;
+        if (sizeof(S) == 8 && fine_wide(L.N)) {
+            k_sell<S, G, E, SU, 1, kFineTPB><<<(int)std::min<long long>(slices, kSM), kFineTPB, 0, s>>>(
+                L.N, F.sptr.p, F.col.p, F.code.p, stencil_of(F), lv.kk, lv.cm, g, e);
+        } else {
+            constexpr int MB = sizeof(S) == 8 ? 4 : 8;  // FP64: fewer, deeper-pipelined threads
+            k_sell<S, G, E, SU, MB><<<(int)std::min<long long>(slices, (long long)kSM * MB), 256, 0, s>>>(
+                L.N, F.sptr.p, F.col.p, F.code.p, stencil_of(F), lv.kk, lv.cm, g, e);
+        }
+        ::bd::note_launch();
         BD_LAUNCH_CHECK();
         return BD_OK;
     }
@@ -1364,8 +1380,8 @@ __global__ void __launch_bounds__(256) k_bsr_reduce(int N, const int *__restrict
 
 // Same with the sliced-ELL finest level.  SU: x is stored as (v + u, u), so a
 // node pair costs two FP64 FMAs (a += Ki s, b += Ke u) instead of three.
-template <int MODE, bool SU>
-__global__ void __launch_bounds__(256, 4) k_sell_reduce(int N, const int *__restrict__ sptr,
+template <int MODE, bool SU, int TPB = 256>
+__global__ void __launch_bounds__(TPB, 1024 / TPB) k_sell_reduce(int N, const int *__restrict__ sptr,
                                                       const int *__restrict__ col,
                                                       const double2 *__restrict__ kk,
                                                       const double *__restrict__ cm,
@@ -1403,7 +1419,7 @@ __global__ void __launch_bounds__(256, 4) k_sell_reduce(int N, const int *__rest
             xs += up;
         }
     }
-    block_finish<MODE == 0 ? 1 : 2, 256>(acc, xs, 0.0, 0.0, fin);
+    block_finish<MODE == 0 ? 1 : 2, TPB>(acc, xs, 0.0, 0.0, fin);
 }
 
 // MODE 0 applies A to the search direction (in (v+u, u) form when the finest
@@ -1415,8 +1431,13 @@ static void fine_reduce(const amg_hierarchy *h, const double2 *x, const double2 
     const Level &L0 = h->lev[0];
     if (h->sell.valid) {
         const FineSell &F = h->sell;
-        k_sell_reduce<MODE, MODE == 0><<<kSM * 4, 256, 0, s>>>(L0.N, F.sptr.p, F.col.p, (const double2 *)F.kk.p,
-                                                                  F.cm.p, x, f, out, fin, d0); ::bd::note_launch();
+        if (fine_wide(L0.N))
+            k_sell_reduce<MODE, MODE == 0, kFineTPB><<<kSM, kFineTPB, 0, s>>>(
+                L0.N, F.sptr.p, F.col.p, (const double2 *)F.kk.p, F.cm.p, x, f, out, fin, d0);
+        else
+            k_sell_reduce<MODE, MODE == 0><<<kSM * 4, 256, 0, s>>>(L0.N, F.sptr.p, F.col.p,
+                                                                  (const double2 *)F.kk.p, F.cm.p, x, f, out, fin, d0);
+        ::bd::note_launch();
         return;
     }
     const BSR &A = L0.A;
@@ -1466,8 +1487,8 @@ struct ZOut {
 // partials in FP64.  That keeps the kernel within 32 registers, so it runs 8
 // blocks per SM like the other FP32 finest-level kernels, which need every
 // resident warp to keep enough bytes in flight.
-template <class S, bool SU, int MINB, class E2>
-__global__ void __launch_bounds__(256, MINB) k_sell_z(int N, const int *__restrict__ sptr,
+template <class S, bool SU, int MINB, class E2, int TPB = 256>
+__global__ void __launch_bounds__(TPB, MINB) k_sell_z(int N, const int *__restrict__ sptr,
                                                     const int *__restrict__ col,
                                                     const unsigned char *__restrict__ code, Stencil st,
                                                     const v2<S> *__restrict__ kk, const S *__restrict__ cm,
@@ -1493,7 +1514,7 @@ __global__ void __launch_bounds__(256, MINB) k_sell_z(int N, const int *__restri
             d = fma(rx, (S)o.x, fma(ry, (S)o.y, d));
         }
     }
-    block_finish<4, 256>((double)a, (double)b, (double)c, (double)d, zo.fin);
+    block_finish<4, TPB>((double)a, (double)b, (double)c, (double)d, zo.fin);
 }
 
 static int zo_streams(const ZOut *zo) { return zo->zold ? 3 : 2; }
@@ -1531,10 +1552,15 @@ static int launch_sell_z(amg_hierarchy *h, const LV<S> &lv, const E2 &epi, const
 {
     const FineSell &F = h->sell;
     const int N = h->lev[0].N;
-    constexpr int MB = sizeof(S) == 8 ? 4 : 8;
-    const int grid = (int)std::min<long long>(((long long)N + 31) / 32, (long long)kSM * MB);
-    k_sell_z<S, SU, MB, E2><<<grid, 256, 0, s>>>(N, F.sptr.p, F.col.p, F.code.p, stencil_of(F), lv.kk, lv.cm,
-                                             GatherVec<S>{lv.d}, epi, zo);
+    const long long slices = ((long long)N + 31) / 32;
+    if (sizeof(S) == 8 && fine_wide(N)) {
+        k_sell_z<S, SU, 1, E2, kFineTPB><<<(int)std::min<long long>(slices, kSM), kFineTPB, 0, s>>>(
+            N, F.sptr.p, F.col.p, F.code.p, stencil_of(F), lv.kk, lv.cm, GatherVec<S>{lv.d}, epi, zo);
+    } else {
+        constexpr int MB = sizeof(S) == 8 ? 4 : 8;
+        k_sell_z<S, SU, MB, E2><<<(int)std::min<long long>(slices, (long long)kSM * MB), 256, 0, s>>>(
+            N, F.sptr.p, F.col.p, F.code.p, stencil_of(F), lv.kk, lv.cm, GatherVec<S>{lv.d}, epi, zo);
+    }
     ::bd::note_launch();
     BD_LAUNCH_CHECK();
     return BD_OK;
