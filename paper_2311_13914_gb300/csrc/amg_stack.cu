@@ -233,6 +233,36 @@ __global__ void __launch_bounds__(256) k_st_sell(int rows, const int *__restrict
     }
 }
 
+// The same for a large FP64 level, as the single hierarchy's finest level runs
+// it: one block of 1024 threads per SM, each block an equal contiguous share of
+// the 32-row slices (the stack's rows are whole slices), rows unrolled deeper
+// with the registers one block per SM leaves.
+template <class S, class E, bool SU>
+__global__ void __launch_bounds__(1024, 1) k_st_sell_wide(int rows, const int *__restrict__ mem,
+                                                          const int *__restrict__ sptr, const int *__restrict__ col,
+                                                          const v2<S> *__restrict__ kk, const S *__restrict__ cm,
+                                                          StGather<S> g, E epi)
+{
+    const long long nsl = ((long long)rows + 31) >> 5;
+    const int lo = (int)(nsl * blockIdx.x / gridDim.x) * 32;
+    const int hi = min(rows, (int)(nsl * (blockIdx.x + 1) / gridDim.x) * 32);
+    for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+        if (mem[p] < 0) continue;
+        const int sl = p >> 5, lane = p & 31, j1 = sptr[sl + 1];
+        S a = 0, b = 0;
+#pragma unroll 8
+        for (int j = sptr[sl]; j < j1; j++) {
+            const size_t idx = (size_t)j * 32 + lane;
+            const v2<S> k = kk[idx];
+            const v2<S> x = g(col[idx]);
+            a = fma(k.x, SU ? x.x : x.x + x.y, a);
+            b = fma(k.y, x.y, b);
+        }
+        const v2<S> xp = g(p);
+        epi(p, fma(cm[p], SU ? xp.x - xp.y : xp.x, a), a + b);
+    }
+}
+
 // ------------------------------------------------------------------ assembly of the stack
 __global__ void k_st_shift(long long n, const int *__restrict__ src, int *__restrict__ dst, int add)
 {
@@ -981,9 +1011,16 @@ int st_apply(const StLevel &Lv, int l, int rows, const S *vals, const v2<S> *x, 
 {
     if (l == 0 && Lv.sell) {
         if (rows <= 0) return BD_OK;
-        const int grid = (int)std::min<long long>(((long long)rows + 255) / 256, (long long)kSM * 8);
-        k_st_sell<S, E, SU><<<grid, 256, 0, s>>>(rows, Lv.mem.p, Lv.ssptr.p, Lv.scol.p, st_kk<S>(Lv), st_cm<S>(Lv),
-                                                 StGather<S>{x}, e);
+        // a large FP64 level: one 1024-thread block per SM on equal shares (measured
+        // against the grid-stride kernel: 64 slabs 2624 -> 2666 solves/s)
+        if (sizeof(S) == 8 && ((long long)rows + 31) / 32 >= (long long)kSM * 32) {
+            k_st_sell_wide<S, E, SU><<<kSM, 1024, 0, s>>>(rows, Lv.mem.p, Lv.ssptr.p, Lv.scol.p, st_kk<S>(Lv),
+                                                          st_cm<S>(Lv), StGather<S>{x}, e);
+        } else {
+            const int grid = (int)std::min<long long>(((long long)rows + 255) / 256, (long long)kSM * 8);
+            k_st_sell<S, E, SU><<<grid, 256, 0, s>>>(rows, Lv.mem.p, Lv.ssptr.p, Lv.scol.p, st_kk<S>(Lv),
+                                                     st_cm<S>(Lv), StGather<S>{x}, e);
+        }
         ::bd::note_launch();
         BD_LAUNCH_CHECK();
         return BD_OK;
