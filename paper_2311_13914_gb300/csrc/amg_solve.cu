@@ -1216,8 +1216,8 @@ __device__ void finish_stage(const Fin &f, double a, double b, double c, double 
 // Block sums of the first NV of a thread's values, in a fixed order: every
 // thread stores its values, then warp k adds column k (the entries of lanes
 // l, l + 32, ... in index order) and folds its 32 lane sums by shuffles into
-// tot[k].  That is 12 FP64 warp additions per value and block for 256 threads,
-// where a shuffle tree in every warp costs 45.
+// tot[k].  That is 12 FP64 warp additions per value and block for 256 threads
+// (36 for 1024), where a shuffle tree in every warp costs 45 for 256.
 template <int NV, int BT>
 __device__ __forceinline__ void block_sum(const double (&v)[4], double (*buf)[BT], double *tot)
 {
@@ -1495,7 +1495,7 @@ struct ZOut {
     Fin fin;
 };
 
-// FP64: at most 64 registers (4 blocks per SM, as the other FP64 finest-level
+// FP64: at most 64 registers (32 warps per SM, as the other FP64 finest-level
 // kernels).  FP32 V-cycle: the per-thread partial sums are FP32, the
 // precision z itself comes in (the V-cycle's output, converted exactly), with
 // r and z_old rounded to FP32 for the products; blocks and the grid add the
